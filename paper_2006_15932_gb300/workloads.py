@@ -1,0 +1,217 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the
+benchmark.
+
+This module holds problem descriptions (grid, species constants, reaction
+and force parameters) and macroscopic initial fields (rho^s, u, T).  It does
+none of the method's arithmetic: the distributions themselves are built by
+whoever consumes a problem (the CUDA library through ``dbm_set_state``, the
+oracle through its own equilibrium routine).
+
+Units are nondimensional: m = 1, T = 1 and unit density give a thermal speed
+of order one.  D2V16 ring speeds and internal speeds default to
+(1.3, 1.2, 2.9, 2.4; 2.2, 0.7, 0.4, 0.3) * sqrt(T_ref / m), which follows the
+paper's guidance (section "Numerical simulation") of placing v near
+sqrt(D T/m) and |u| and eta near sqrt(I T/m); its moment matrix has a
+condition number of about 4e2.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import List, Sequence
+
+import numpy as np
+
+PERIODIC, OUTFLOW = 0, 1
+SEED = 20200627
+
+DEFAULT_V = (1.3, 1.2, 2.9, 2.4)
+DEFAULT_ETA = (2.2, 0.7, 0.4, 0.3)
+
+
+@dataclass
+class SpeciesSpec:
+    m: float = 1.0
+    I: float = 3.0
+    tau: float = 2e-5
+    v: Sequence[float] = DEFAULT_V
+    eta: Sequence[float] = DEFAULT_ETA
+    a: float = 0.0
+
+
+def species(m=1.0, I=3.0, tau=2e-5, a=0.0, T_ref=1.0, v=DEFAULT_V, eta=DEFAULT_ETA) -> SpeciesSpec:
+    s = math.sqrt(T_ref / m)
+    return SpeciesSpec(m=m, I=I, tau=tau, v=tuple(x * s for x in v), eta=tuple(x * s for x in eta), a=a)
+
+
+@dataclass
+class Problem:
+    name: str
+    nx: int
+    ny: int
+    species: List[SpeciesSpec]
+    dx: float = 1e-3
+    dy: float = 1e-3
+    dt: float = 1e-5
+    bc_x: int = PERIODIC
+    bc_y: int = PERIODIC
+    fuel: int = 0
+    oxid: int = 1
+    k_ov: float = 0.0
+    Ea_over_R: float = 0.0
+    Q: float = 0.0
+    accel: tuple = (0.0, 0.0)
+    nsteps: int = 1
+    # macroscopic initial fields: rho_s (S, ny, nx), ux/uy/T (ny, nx)
+    rho_s: np.ndarray = None
+    ux: np.ndarray = None
+    uy: np.ndarray = None
+    T: np.ndarray = None
+
+    @property
+    def ns(self) -> int:
+        return len(self.species)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny
+
+
+def to_oracle_params(pb: Problem):
+    """The oracle's parameter record for a problem (test side only)."""
+    from oracle import oracle as O
+
+    sp = [O.Species(m=s.m, I=s.I, tau=s.tau, v=tuple(s.v), eta=tuple(s.eta), a=s.a) for s in pb.species]
+    return O.Params(nx=pb.nx, ny=pb.ny, species=sp, dx=pb.dx, dy=pb.dy, dt=pb.dt, bc_x=pb.bc_x,
+                    bc_y=pb.bc_y, fuel=pb.fuel, oxid=pb.oxid, k_ov=pb.k_ov, Ea_over_R=pb.Ea_over_R,
+                    Q=pb.Q, accel=tuple(pb.accel))
+
+
+# ---------------------------------------------------------------------------
+# configurations
+# ---------------------------------------------------------------------------
+
+def sod_tube(nx: int = 400, nsteps: int = 2000) -> Problem:
+    """Sod-type shock tube, two non-reacting species with mass fractions
+    0.5/0.5 (m = 1, I = 3, so gamma = 1.4): rho = 1, p = 1 for x < 0.2,
+    rho = 0.125, p = 0.1 beyond, u = 0; dx = 1e-3 (for 400 cells), dt = 1e-5,
+    tau = 2e-5; outflow in x, periodic in y with one row."""
+    L = 0.4
+    dx = L / nx
+    x = (np.arange(nx) + 0.5) * dx
+    left = x < 0.2
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    sp = [species(m=1.0, I=3.0, tau=2e-5), species(m=1.0, I=3.0, tau=2e-5)]
+    n = rho / 1.0
+    T = p / n
+    rho_s = np.stack([0.5 * rho, 0.5 * rho])[:, None, :]
+    return Problem(name="sod_400x1_s2", nx=nx, ny=1, species=sp, dx=dx, dy=dx, dt=1e-5 * dx / 1e-3,
+                   bc_x=OUTFLOW, bc_y=PERIODIC, nsteps=nsteps, rho_s=rho_s,
+                   ux=np.zeros((1, nx)), uy=np.zeros((1, nx)), T=T[None, :])
+
+
+def random_smooth(nx: int, ny: int, ns: int, seed: int = SEED, *, reactive: bool = False,
+                  force: bool = False, bc=(PERIODIC, PERIODIC), amp: float = 0.05,
+                  unequal: bool = True, dt: float = 1e-5, tau: float = 2e-5) -> Problem:
+    """A smooth random state of ns species on an nx x ny grid: a few random
+    Fourier modes of amplitude ``amp`` on density, velocity and temperature
+    around rho^s = 1/ns, u = (0.1, -0.05), T = 1.  Unequal masses and
+    relaxation times when ``unequal``.  With ``reactive`` species 0 is the
+    fuel, 1 the oxidiser and the rest products (a = -1, -1, +2/(ns-2)...,
+    chosen with equal masses so that sum a m = 0)."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.meshgrid(np.arange(ny) / max(ny, 1), np.arange(nx) / max(nx, 1), indexing="ij")
+
+    def field(base, a):
+        out = np.full((ny, nx), base, dtype=np.float64)
+        for _ in range(3):
+            kx, ky = rng.integers(1, 4, size=2)
+            ph = rng.uniform(0, 2 * math.pi)
+            out += a * base * rng.uniform(0.3, 1.0) * np.sin(2 * math.pi * (kx * xx + ky * yy) + ph)
+        return out
+
+    sp = []
+    for s in range(ns):
+        m = (1.0 + 0.5 * s) if (unequal and not reactive) else 1.0
+        t = tau * ((1.0 + 0.25 * s) if unequal else 1.0)
+        sp.append(species(m=m, I=3.0 + (s % 2) if unequal else 3.0, tau=t))
+    if reactive:
+        assert ns >= 3
+        sp[0].a, sp[1].a = -1.0, -1.0
+        for s in range(2, ns):
+            sp[s].a = 2.0 / (ns - 2)
+    rho_s = np.stack([field(1.0 / ns, amp) for _ in range(ns)])
+    ux = field(0.1, amp)
+    uy = field(-0.05, amp)
+    T = field(1.0, amp)
+    pb = Problem(name=f"random_{nx}x{ny}_s{ns}", nx=nx, ny=ny, species=sp, dx=1e-3, dy=1e-3, dt=dt,
+                 bc_x=bc[0], bc_y=bc[1], rho_s=rho_s, ux=ux, uy=uy, T=T)
+    if reactive:
+        pb.fuel, pb.oxid = 0, 1
+        pb.k_ov = 2.0e3
+        pb.Ea_over_R = 2.0
+        pb.Q = 1.5
+    if force:
+        pb.accel = (30.0, -50.0)
+    return pb
+
+
+def reactive_premixed(nx: int = 1024, ny: int = 256, seed: int = SEED, nsteps: int = 20000) -> Problem:
+    """Premixed 2-D reactive gas, three species (fuel F, oxidiser O, product
+    P), one-step reaction F + O -> 2 P (a = -1, -1, +2; m = 1 each):
+    mass fractions 0.5/0.5/0 (product 1e-3 seed), rho = 1, T = 1, u = 0,
+    +-1% seeded white noise on density at constant pressure; a hot product
+    band at x < nx/16 ignites it.  Periodic in x and y; dx = 1e-3,
+    dt = 1e-5, tau = 2e-5.  Reaction constants are drawn from a seed in
+    ranges that give visible conversion within 20k steps."""
+    rng = np.random.default_rng(seed)
+    sp = [species(tau=2e-5, a=-1.0), species(tau=2e-5, a=-1.0), species(tau=2e-5, a=2.0)]
+    noise = rng.uniform(-0.01, 0.01, size=(ny, nx))
+    rho = 1.0 + noise
+    T = 1.0 / rho  # constant pressure p = n T = 1
+    x = np.arange(nx)[None, :] * np.ones((ny, 1))
+    hot = x < nx // 16
+    yF = np.where(hot, 0.05, 0.4995)
+    yO = np.where(hot, 0.05, 0.4995)
+    yP = 1.0 - yF - yO
+    T = np.where(hot, 1.8 / rho, T)
+    rho_s = np.stack([rho * yF, rho * yO, rho * yP])
+    k_ov = float(rng.uniform(20.0, 40.0))
+    Ea = float(rng.uniform(2.0, 3.0))
+    Q = float(rng.uniform(0.6, 0.9))
+    return Problem(name=f"reactive_{nx}x{ny}_s3", nx=nx, ny=ny, species=sp, dx=1e-3, dy=1e-3, dt=1e-5,
+                   bc_x=PERIODIC, bc_y=PERIODIC, fuel=0, oxid=1, k_ov=k_ov, Ea_over_R=Ea, Q=Q,
+                   nsteps=nsteps, rho_s=rho_s, ux=np.zeros((ny, nx)), uy=np.zeros((ny, nx)), T=T)
+
+
+def kh_shear_layer(n: int = 4096, seed: int = SEED, ny: int | None = None) -> Problem:
+    """Kelvin-Helmholtz shear layer with the paper's geometry (section
+    "Kelvin-Helmholtz instability"): two species, u_y = 0.5 tanh((x-x0)/w)
+    with w = 8 dx, species mass fraction following the same tanh, interface
+    x0(y) = nx/2 + A sin(2 pi y / ny) with A = 4 dx and a seeded phase;
+    uniform p = 1 and T = 1; outflow in x, periodic in y; dx = 1e-3,
+    dt = 1e-5, tau = 2e-5."""
+    rng = np.random.default_rng(seed)
+    nx = n
+    ny = n if ny is None else ny
+    ph = float(rng.uniform(0, 2 * math.pi))
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    x0 = nx / 2 + 4.0 * np.sin(2 * math.pi * y / ny + ph)
+    t = np.tanh((x - x0) / 8.0)
+    uy = 0.5 * t
+    y1 = 0.5 * (1.0 + t)
+    rho = np.ones((ny, nx))
+    rho_s = np.stack([rho * (1.0 - y1), rho * y1])
+    sp = [species(m=1.0, tau=2e-5), species(m=1.0, tau=2e-5)]
+    return Problem(name=f"kh_{nx}x{ny}_s2", nx=nx, ny=ny, species=sp, dx=1e-3, dy=1e-3, dt=1e-5,
+                   bc_x=OUTFLOW, bc_y=PERIODIC, nsteps=1000, rho_s=rho_s,
+                   ux=np.zeros((ny, nx)), uy=uy, T=np.ones((ny, nx)))
+
+
+def uniform(nx: int, ny: int, sp: List[SpeciesSpec], rho_s, ux=0.0, uy=0.0, T=1.0, **kw) -> Problem:
+    rho_s = np.asarray(rho_s, dtype=np.float64)[:, None, None] * np.ones((1, ny, nx))
+    return Problem(name=f"uniform_{nx}x{ny}", nx=nx, ny=ny, species=sp, rho_s=rho_s,
+                   ux=np.full((ny, nx), float(ux)), uy=np.full((ny, nx), float(uy)),
+                   T=np.full((ny, nx), float(T)), **kw)
