@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Throughput of the fused D2V16 DBM step on GB300.
+
+Default workload: the Kelvin-Helmholtz shear layer on 4096 x 4096 cells with
+2 species, f stored and stepped in FP32 (the largest single-grid
+configuration), synthetic seeded initial fields, one fused kernel launch
+per time step.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                  [--workload kh4096|reactive|sod] [--precision fp32|fp64]
+
+N > 1 runs under torchrun: every rank steps its own replica of the grid
+(independent problems, no data-path collective) and the value is the sum of
+all ranks' updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2V16 species-cell updates/s and HBM-roofline %, FP32 vs FP64; serve p50/p99"
+UNIT = "species-cell updates/s"
+BYTES_PER_UPDATE = {"fp64": 256, "fp32": 128}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="kh4096", choices=["kh4096", "reactive", "sod"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and e2e side legs")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--grid", default=None, help="override the grid, e.g. 2048x1024 (profiling runs)")
+    return ap.parse_args()
+
+
+def make_workload(name, grid=None):
+    from paper_2006_15932_gb300 import workloads as W
+
+    nx, ny = (int(v) for v in grid.lower().split("x")) if grid else (None, None)
+    if name == "kh4096":
+        return W.kh_shear_layer(nx or 4096, ny=ny)
+    if name == "reactive":
+        return W.reactive_premixed(nx or 1024, ny or 256)
+    return W.sod_tube(nx or 400, 2000)
+
+
+def workload_config(pb, name, precision):
+    return {
+        "workload": {"kh4096": "kelvin_helmholtz_shear_layer", "reactive": "reactive_premixed_2d",
+                     "sod": "sod_shock_tube"}[name],
+        "grid": [pb.nx, pb.ny],
+        "species": pb.ns,
+        "velocities": 16,
+        "precision": precision,
+        "reactive": pb.k_ov != 0.0,
+        "boundary": ["periodic" if b == 0 else "outflow" for b in (pb.bc_x, pb.bc_y)],
+        "state_bytes_per_buffer": pb.nx * pb.ny * pb.ns * 16 * (8 if precision == "fp64" else 4),
+        "l2_policy": "inputs larger than L2" if pb.nx * pb.ny * pb.ns * 64 > 129e6
+        else "state fits in L2 (no flush)",
+    }
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for rel in ("paper_2006_15932_gb300/csrc/dbm_step_impl.cuh", "paper_2006_15932_gb300/csrc/dbm_device.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(name, precision):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "step_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    key = f"{name}:{precision}"
+    e = d.get(key)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            out_dir = os.path.join(ROOT, "gpurun_out")
+            os.makedirs(out_dir, exist_ok=True)
+            self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and self.uuid not in parts[1]:
+                continue
+            try:
+                sm.append(float(parts[2].split()[0]))
+                smax.append(float(parts[3].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(pb_full, precision, seconds):
+    """The FP64 oracle as it stands, on the host cores, over a bounded
+    sample of the workload: a window of the same grid (same species,
+    parameters and initial fields) stepped a few times."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2006_15932_gb300 import workloads as W
+
+    nx = min(pb_full.nx, 512)
+    ny = min(pb_full.ny, 256)
+    x0 = (pb_full.nx - nx) // 2
+    y0 = (pb_full.ny - ny) // 2
+    pb = W.Problem(name=pb_full.name + "_window", nx=nx, ny=ny, species=pb_full.species, dx=pb_full.dx,
+                   dy=pb_full.dy, dt=pb_full.dt, bc_x=pb_full.bc_x, bc_y=pb_full.bc_y, fuel=pb_full.fuel,
+                   oxid=pb_full.oxid, k_ov=pb_full.k_ov, Ea_over_R=pb_full.Ea_over_R, Q=pb_full.Q,
+                   accel=pb_full.accel, rho_s=pb_full.rho_s[:, y0:y0 + ny, x0:x0 + nx],
+                   ux=pb_full.ux[y0:y0 + ny, x0:x0 + nx], uy=pb_full.uy[y0:y0 + ny, x0:x0 + nx],
+                   T=pb_full.T[y0:y0 + ny, x0:x0 + nx])
+    p = W.to_oracle_params(pb)
+    f = O.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
+    t0 = time.perf_counter()
+    f, _ = O.run(p, f, 1)
+    t1 = time.perf_counter()
+    per_step = max(t1 - t0, 1e-6)
+    steps = max(1, min(200, int(seconds / per_step)))
+    t0 = time.perf_counter()
+    O.run(p, f, steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": nx * ny * pb.ns * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nx}x{ny} window of the {pb_full.nx}x{pb_full.ny} grid, {pb.ns} species, "
+                      f"{steps} FP64 steps in {dt:.1f} s (OpenMP over rows)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    pb = make_workload(args.workload, args.grid)
+    cfg = workload_config(pb, args.workload, args.precision)
+    # each "step" of the reference arm is a bounded sample of the workload
+    per = max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(pb, args.precision, per / 4)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(pb, args.precision, per))
+    wall = time.perf_counter() - t0
+    value = statistics.median(v["value"] for v in vals)
+    cb = dict(vals[-1])
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2006_15932_gb300 import build as B
+    from paper_2006_15932_gb300 import dbm as D
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    D.load()
+
+    pb = make_workload(args.workload, args.grid)
+    cfg = workload_config(pb, args.workload, args.precision)
+    stream = torch.cuda.Stream(device=dev)
+    solver = D.Solver(pb, args.precision, device=dev, stream=stream)
+    with torch.cuda.stream(stream):
+        solver.set_state()
+        for _ in range(max(args.warmup, 3)):
+            solver.step(1)
+    torch.cuda.synchronize(dev)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.25)  # let the sampler start
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(K):
+            solver.step(1)
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+    ms_total = ev[0].elapsed_time(ev[K])
+    rc, bits = solver.status()
+    if rc != 0:
+        raise SystemExit(f"health flag raised during the benchmark: rc={rc} bits={bits}")
+    ms = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    ms_max = float(ms.item())
+    updates_per_rank = pb.nx * pb.ny * pb.ns * K
+    value = updates_per_rank * world / (ms_max * 1e-3)
+
+    peak, peak_kind = measured_peaks()
+    bpu = BYTES_PER_UPDATE[args.precision]
+    avg_launch_ms = statistics.mean(per_launch)
+    bytes_per_launch = pb.nx * pb.ny * pb.ns * bpu
+    achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
+    traffic = ncu_traffic(args.workload, args.precision)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel": f"k_step<{'float' if args.precision == 'fp32' else 'double'},{pb.ns}>",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "median_launch_ms": statistics.median(per_launch)}
+
+    extras = {}
+    e2e = None
+    if not args.no_extras:
+        e2e = measure_e2e(D, pb, args.precision, dev, stream)
+        if args.precision == "fp32" and rank == 0:
+            extras["fp64"] = measure_fp64(D, pb, dev, stream)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic (seeded analytic initial fields)", "config": cfg, "roofline": roofline,
+            "clocks": clk, "gpu_launches": K, "e2e": e2e}
+    line.update(extras)
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(pb, args.precision, args.cpu_seconds)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_e2e(D, pb, precision, dev, stream, n_inner=50, reps=3):
+    """End to end through the public API: pinned host fields -> device,
+    dbm_set_state, n_inner dbm_step, dbm_moments, moments -> pinned host.
+    Every solve copies its inputs in and its result out."""
+    import torch
+
+    host = [torch.from_numpy(a.astype("float64")).pin_memory() for a in (pb.rho_s, pb.ux, pb.uy, pb.T)]
+    out_host = torch.empty((4 * pb.ns + 5, pb.ny, pb.nx), dtype=torch.float64).pin_memory()
+    solver = D.Solver(pb, precision, device=dev, stream=stream)
+    dev_in = [torch.empty(h.shape, dtype=torch.float64, device=dev) for h in host]
+    dev_out = torch.empty(out_host.shape, dtype=torch.float64, device=dev)
+
+    def once():
+        with torch.cuda.stream(stream):
+            for d, h in zip(dev_in, host):
+                d.copy_(h, non_blocking=True)
+            solver.set_state(*dev_in)
+            solver.step(n_inner)
+            solver.moments(dev_out)
+            out_host.copy_(dev_out, non_blocking=True)
+        stream.synchronize()
+
+    once()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        once()
+    dt = (time.perf_counter() - t0) / reps
+    solver.close()
+    h2d = sum(h.numel() * 8 for h in host)
+    d2h = out_host.numel() * 8
+    return {"value": pb.nx * pb.ny * pb.ns * n_inner / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h,
+            "step": f"one solve: host fields in, dbm_set_state, {n_inner} dbm_step, dbm_moments, host out"}
+
+
+def measure_fp64(D, pb, dev, stream, steps=10):
+    import torch
+
+    s = D.Solver(pb, "fp64", device=dev, stream=stream)
+    with torch.cuda.stream(stream):
+        s.set_state()
+        s.step(2)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        s.step(steps)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    s.close()
+    upd = pb.nx * pb.ny * pb.ns / (ms * 1e-3)
+    return {"value": upd, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "hbm_frac_of_measured": upd * BYTES_PER_UPDATE["fp64"] / 1e9 / measured_peaks()[0],
+            "bound": "alu (FP64 pipe)"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * dbm.h -- C ABI of the GB300 (sm_103a) solver for the multi-component
+ * discrete Boltzmann model (DBM) of Lin, Luo, Fei & Succi, "A multi-component
+ * discrete Boltzmann model for nonequilibrium reactive flows"
+ * (arXiv 2006.15932), on its two-dimensional sixteen-velocity (D2V16) set.
+ *
+ * One call of dbm_step advances the species distributions f^s_i of every
+ * cell by forward-Euler steps of the discrete Boltzmann equation (Eq.
+ * DiscreteBoltzmannEquation):
+ *     f^{n+1} = f^n + dt [ Omega + R + G - v_i . grad f^n ],
+ * Omega = BGK collision (Eq. CollisionTerm), R = reaction (Eq. ReactionTerm),
+ * G = force (Eq. ForceTerm), with the equilibria f^eq = M^-1 f-hat built from
+ * the moment relations relation1..relation7, and the advection discretised by
+ * the NND scheme (section "Numerical simulation").
+ *
+ * Conventions
+ *  - Every call returns int: DBM_OK (0) or a negative dbm_status_code.
+ *    Nothing is thrown across the ABI.  dbm_last_error() gives a message.
+ *  - The library owns only the handle (host memory) and the per-species
+ *    constants it derives (carried in kernel parameters).  The caller owns
+ *    every device buffer and every stream; no call allocates device memory.
+ *  - "stream" arguments are cudaStream_t values passed as void* (NULL is the
+ *    legacy default stream).  Calls marked async only enqueue work.
+ *  - Field arrays exchanged with the caller are dense FP64, x fastest:
+ *    a scalar field is [ny][nx], a species field [S][ny][nx], a distribution
+ *    [S][16][ny][nx].  They may live in device memory or in page-locked host
+ *    memory that the device can address (cudaHostAlloc / cudaHostRegister);
+ *    pageable host memory is not accepted.
+ *  - Velocity index i = 0..15 runs over the rings a, b, c, d (4 each) in the
+ *    order of the D2V16 definition: axis rings (v,0), (0,v), (-v,0), (0,-v);
+ *    diagonal rings (v,v), (-v,v), (-v,-v), (v,-v).
+ */
+#ifndef DBM_H
+#define DBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DBM_Q 16
+#define DBM_MAX_SPECIES 8
+
+enum dbm_bc { DBM_BC_PERIODIC = 0, DBM_BC_OUTFLOW = 1 };
+
+/* Arithmetic and storage of the stepped state.
+ *  DBM_FP64    f stored and stepped in double.
+ *  DBM_FP32    f stored and stepped in float; the mixture temperature (from
+ *              the energy moment), the Arrhenius rate and all reported
+ *              outputs are computed in double.
+ *  DBM_BF16DEV f stored as a bfloat16 deviation from the equilibrium of
+ *              stored float moments (n^s, u, T), stepped in float. */
+enum dbm_precision { DBM_FP64 = 0, DBM_FP32 = 1, DBM_BF16DEV = 2 };
+
+enum dbm_status_code {
+    DBM_OK = 0,
+    DBM_ERR_INVALID = -1,     /* a parameter or argument is out of range      */
+    DBM_ERR_SINGULAR = -2,    /* a moment matrix M is singular/ill-conditioned */
+    DBM_ERR_UNBOUND = -3,     /* state buffers not bound yet                   */
+    DBM_ERR_CUDA = -4,        /* a CUDA runtime call or launch failed           */
+    DBM_ERR_NONFINITE = -5,   /* device health flag: a non-finite moment        */
+    DBM_ERR_NEGATIVE = -6,    /* device health flag: n^s <= 0, T <= 0 or n* < 0 */
+    DBM_ERR_STABILITY = -7    /* CFL or dt/tau stability limit exceeded         */
+};
+
+/* Health-flag bits as kept on the device (dbm_status_bits). */
+enum dbm_health_bits {
+    DBM_HEALTH_DENSITY = 1,      /* n^s <= 0 or not finite      */
+    DBM_HEALTH_TEMPERATURE = 2,  /* mixture T <= 0 or not finite */
+    DBM_HEALTH_NSTAR = 4,        /* n^s* < 0 after the reaction  */
+    DBM_HEALTH_NONFINITE = 8     /* a non-finite moment           */
+};
+
+/* Constants of one species sigma. */
+typedef struct dbm_species {
+    double m;        /* molar mass m^s (> 0)                                    */
+    double I;        /* extra degrees of freedom I^s (>= 0); gamma = (D+I+2)/(D+I) */
+    double tau;      /* relaxation time tau^s (> 0)                              */
+    double v[4];     /* ring speeds v_a, v_b, v_c, v_d (> 0)                     */
+    double eta[4];   /* internal speeds eta_a .. eta_d (>= 0, not all 0)         */
+    double a_stoich; /* stoichiometric coefficient a^s of the one-step reaction  */
+} dbm_species;
+
+/* Problem description (section "Discrete Boltzmann model" for the physics,
+ * section "Numerical simulation" for the discretisation). */
+typedef struct dbm_params {
+    int nx, ny;             /* interior cells (>= 1 each)                          */
+    int nspecies;           /* S, 1 .. DBM_MAX_SPECIES                              */
+    double dx, dy, dt;      /* grid spacing and time step (> 0)                     */
+    int bc_x, bc_y;         /* dbm_bc per axis: periodic, or outflow (zero-gradient) */
+    int fuel, oxidizer;     /* species indices of the Arrhenius rate               */
+    double k_ov;            /* reaction coefficient; 0 switches the reaction off   */
+    double Ea_over_R;       /* activation temperature E_a / R                       */
+    double Q;               /* heat released per mole of reaction                   */
+    double accel[2];        /* external acceleration a of the force term; 0 = off   */
+    int precision;          /* dbm_precision                                         */
+    dbm_species sp[DBM_MAX_SPECIES];
+} dbm_params;
+
+/* Device storage geometry of one state buffer: plane p = s*16 + i holds
+ * `rows` rows of `pitch` elements; interior cell (x, y) sits at element
+ * p*plane + (y + gy)*pitch + (x + gx).  Ghost cells fill the margins.
+ * For DBM_BF16DEV the buffer holds 16*S bfloat16 deviation planes followed
+ * (at byte offset moments_offset) by S+3 float moment planes
+ * (n^0..n^{S-1}, u_x, u_y, T) of the same geometry. */
+typedef struct dbm_layout {
+    int pitch, rows, gx, gy;
+    long long plane;          /* elements per plane                       */
+    int elem_bytes;           /* bytes per stored f element (8, 4 or 2)   */
+    size_t moments_offset;    /* BF16DEV only: byte offset of the moments */
+    size_t bytes;             /* bytes of one state buffer                */
+} dbm_layout;
+
+typedef struct dbm_handle dbm_handle;
+
+/* Validate params, build M^s for every species (rows of the M_ki list, row 9
+ * read as (v^2+eta^2) v_y) and invert it on the host in FP64 (LU with
+ * partial pivoting).  Rejects: S outside 1..8, non-positive sizes, m, tau,
+ * dx, dy, dt or ring speeds; a singular M, or an infinity-norm condition
+ * number of the row-equilibrated M above 1e8 (DBM_ERR_SINGULAR); with the reaction on, bad fuel/oxidizer indices or
+ * |sum_s a^s m^s| > 1e-12 sum_s |a^s m^s| (DBM_ERR_INVALID); a CFL number
+ * max|v_ia| dt / d_a > 0.5 or dt >= 2 tau^s (DBM_ERR_STABILITY).
+ * On success *out owns a new handle (free with dbm_destroy). */
+int dbm_init(const dbm_params *params, dbm_handle **out);
+
+/* Message of the last failed dbm_init on the calling thread ("" after a
+ * successful one). */
+const char *dbm_init_error(void);
+
+/* Storage geometry and size of one state buffer for this handle. */
+int dbm_get_layout(const dbm_handle *h, dbm_layout *out);
+
+/* Bytes of one state buffer (the caller allocates two) and of the scratch
+ * buffer (health flag and reduction partials). */
+int dbm_state_bytes(const dbm_handle *h, size_t *bytes);
+int dbm_scratch_bytes(const dbm_handle *h, size_t *bytes);
+
+/* Bind caller-owned device buffers: f_a and f_b of dbm_state_bytes each
+ * (256-byte aligned), scratch of dbm_scratch_bytes.  f_a becomes the current
+ * state.  The buffers must outlive every call that uses them. */
+int dbm_bind(dbm_handle *h, void *f_a, void *f_b, void *scratch);
+
+/* f = f^eq(n^s = rho^s / m^s, u, T) in every cell from the macroscopic
+ * fields rho_s [S][ny][nx], ux, uy, T [ny][nx] (FP64); ghosts filled; health
+ * flag cleared.  Async on stream. */
+int dbm_set_state(dbm_handle *h, const double *rho_s, const double *ux, const double *uy,
+                  const double *T, void *stream);
+
+/* Load / read the raw distributions, dense FP64 [S][16][ny][nx] (checkpoint
+ * and restore).  dbm_set_f fills the ghosts and clears the health flag;
+ * in DBM_BF16DEV mode it stores the moments of f and the bfloat16 deviation
+ * from their equilibrium, and dbm_get_f reconstructs f.  Async on stream. */
+int dbm_set_f(dbm_handle *h, const double *f, void *stream);
+int dbm_get_f(dbm_handle *h, double *f, void *stream);
+
+/* Advance nsteps >= 0 forward-Euler steps (Eqs. DiscreteBoltzmannEquation,
+ * CollisionTerm, ReactionTerm, ForceTerm; NND advection).  One fused kernel
+ * launch per step; ghosts of the new state are written by the same kernel.
+ * Async on stream; never synchronises and never allocates. */
+int dbm_step(dbm_handle *h, int nsteps, void *stream);
+
+/* Macroscopic fields of the current state, FP64 out[(4S+5)][ny][nx]:
+ *   rows 4s..4s+3: n^s, u^s_x, u^s_y, T^s = m^s (E^s/n^s - u^s.u^s)/(D+I^s);
+ *   rows 4S..4S+4: rho = sum m^s n^s, u_x, u_y, T (mixture, from conservation
+ *   of the collision term), p = n T with n = sum n^s.  Async on stream. */
+int dbm_moments(dbm_handle *h, double *out, void *stream);
+
+/* Nonequilibrium moments, FP64 out[20 S][ny][nx], 20 rows per species s
+ * (Eqs. Delta2, Delta31, Delta3, Delta42 and the energy diagnostics defined
+ * after them; f^eq = f^eq(n^s, u, T) with the mixture u, T):
+ *   0..2 Delta_2 xx, xy, yy       3..4 Delta_3,1 x, y
+ *   5..8 Delta_3 xxx, xxy, xyy, yyy   9..11 Delta_4,2 xx, xy, yy
+ *   12..13 M_2xx(f)/2, M_2yy(f)/2     14..15 M_2xx(f^eq)/2, M_2yy(f^eq)/2
+ *   16..17 M_3,1x(f)/2, M_3,1y(f)/2   18..19 M_3,1x(f^eq)/2, M_3,1y(f^eq)/2
+ * All sums carry the factor m^s.  Async on stream. */
+int dbm_nonequilibrium(dbm_handle *h, double *out, void *stream);
+
+/* Conserved totals over the interior cells, FP64 out[S+4] (device or
+ * addressable host memory): out[s] = sum rho^s; out[S], out[S+1] = sum rho u;
+ * out[S+2] = total energy sum_s (m^s/2) sum_i f (v.v + eta^2);
+ * out[S+3] = sum Q n^fuel / |a^fuel| (heat still bound in the fuel; 0
+ * without reaction).  Summed in FP64 in a fixed order (deterministic).
+ * Uses the bound scratch buffer.  Async on stream. */
+int dbm_conservation(dbm_handle *h, double *out, void *stream);
+
+/* Synchronise the stream, read the sticky device health flag and map it to
+ * DBM_OK, DBM_ERR_NEGATIVE or DBM_ERR_NONFINITE.  *bits (may be NULL)
+ * receives the raw dbm_health_bits. */
+int dbm_status(dbm_handle *h, void *stream, unsigned *bits);
+
+/* Steps taken since the last dbm_set_state / dbm_set_f. */
+long long dbm_steps_taken(const dbm_handle *h);
+
+/* Message of the last failed call on this handle ("" if none).  The string
+ * is owned by the handle. */
+const char *dbm_last_error(const dbm_handle *h);
+
+/* Release the handle (not the caller's buffers).  NULL is allowed. */
+void dbm_destroy(dbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBM_H */

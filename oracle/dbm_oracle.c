@@ -409,11 +409,13 @@ int orc_prepare(const orc_params *p, double *Minv)
 
 /* New f of the cells (x, y) with x0 <= x < x1 and y0 <= y < y1 after one
  * forward-Euler step: f^{n+1} = f^n + dt [Omega + R + G - d(v_x f)/dx -
- * d(v_y f)/dy], everything on the right taken at time n.  fout has the
- * layout of fin.  Returns status bits. */
+ * d(v_y f)/dy], everything on the right taken at time n.  fin is the whole
+ * field; fout holds only the region, [s][i][y - y0][x - x0].  Returns
+ * status bits. */
 int orc_step_region(const orc_params *p, const double *Minv, const double *fin, double *fout,
                     int x0, int x1, int y0, int y1)
 {
+    const int rw = x1 - x0, rh = y1 - y0;
     const int ns = p->ns;
     int status = ORC_OK;
 #pragma omp parallel for schedule(static) reduction(| : status)
@@ -442,7 +444,7 @@ int orc_step_region(const orc_params *p, const double *Minv, const double *fin, 
                     }
                     const double fnew = fc[s * ORC_Q + i] + p->dt * (rhs[s * ORC_Q + i] - adv);
                     if (!isfinite(fnew)) status |= ORC_NONFINITE;
-                    fout[fidx(p, s, i, x, y)] = fnew;
+                    fout[(((size_t)s * ORC_Q + i) * rh + (y - y0)) * rw + (x - x0)] = fnew;
                 }
             }
         }

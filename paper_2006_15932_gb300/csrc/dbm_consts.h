@@ -1,0 +1,94 @@
+// dbm_consts.h -- fill the kernel-parameter blocks from a validated handle.
+#pragma once
+
+#include <math.h>
+#include <string.h>
+
+#include "dbm_internal.h"
+
+namespace dbm {
+
+// v.v + eta^2 of ring r: |v|^2 = v_r^2 on the axis rings, 2 v_r^2 on the
+// diagonal rings.
+inline double ring_q(const dbm_species &sp, int r)
+{
+    const double v2 = sp.v[r] * sp.v[r] * ((r & 1) ? 2.0 : 1.0);
+    return v2 + sp.eta[r] * sp.eta[r];
+}
+
+template <typename real, int S>
+void fill_step_consts(const dbm_handle *h, StepConsts<real, S> &c)
+{
+    memset(&c, 0, sizeof(c));
+    const dbm_params &p = h->p;
+    for (int s = 0; s < S; ++s) {
+        const dbm_species &sp = p.sp[s];
+        for (int i = 0; i < Q; ++i)
+            for (int k = 0; k < Q; ++k) c.cinv[s][i][k] = (real)h->cinv[s][i][k];
+        for (int r = 0; r < 4; ++r) {
+            c.vr[s][r] = (real)sp.v[r];
+            c.qr[s][r] = (real)ring_q(sp, r);
+        }
+        c.m[s] = (real)sp.m;
+        c.inv_tau[s] = (real)(1.0 / sp.tau);
+        c.dpi[s] = (real)(2.0 + sp.I);
+        c.tau[s] = (real)sp.tau;
+        c.a[s] = (real)sp.a_stoich;
+        c.m_d[s] = sp.m;
+        c.inv_tau_d[s] = 1.0 / sp.tau;
+        c.dpi_d[s] = 2.0 + sp.I;
+        c.tau_d[s] = sp.tau;
+        c.a_d[s] = sp.a_stoich;
+    }
+    c.dt = (real)p.dt;
+    c.dt_dx = (real)(p.dt / p.dx);
+    c.dt_dy = (real)(p.dt / p.dy);
+    c.accel_x = (real)p.accel[0];
+    c.accel_y = (real)p.accel[1];
+    c.k_ov = p.k_ov;
+    c.Ea_over_R = p.Ea_over_R;
+    c.Qheat = p.Q;
+    c.fuel = p.fuel;
+    c.oxid = p.oxidizer;
+    c.has_reaction = p.k_ov != 0.0;
+    c.has_force = p.accel[0] != 0.0 || p.accel[1] != 0.0;
+    c.nx = p.nx;
+    c.ny = p.ny;
+    c.pitch = h->lay.pitch;
+    c.bc_x = p.bc_x;
+    c.bc_y = p.bc_y;
+    c.plane = h->lay.plane;
+}
+
+template <int S>
+void fill_out_consts(const dbm_handle *h, OutConsts<S> &c)
+{
+    memset(&c, 0, sizeof(c));
+    const dbm_params &p = h->p;
+    for (int s = 0; s < S; ++s) {
+        const dbm_species &sp = p.sp[s];
+        for (int i = 0; i < Q; ++i)
+            for (int k = 0; k < Q; ++k) c.cinv[s][i][k] = h->cinv[s][i][k];
+        for (int r = 0; r < 4; ++r) {
+            c.vr[s][r] = sp.v[r];
+            c.qr[s][r] = ring_q(sp, r);
+            c.eta[s][r] = sp.eta[r];
+        }
+        c.m[s] = sp.m;
+        c.inv_tau[s] = 1.0 / sp.tau;
+        c.dpi[s] = 2.0 + sp.I;
+        c.a[s] = sp.a_stoich;
+    }
+    c.has_reaction = p.k_ov != 0.0;
+    c.fuel = p.fuel;
+    c.Qheat = p.Q;
+    c.abs_a_fuel = c.has_reaction ? fabs(p.sp[p.fuel].a_stoich) : 1.0;
+    c.nx = p.nx;
+    c.ny = p.ny;
+    c.pitch = h->lay.pitch;
+    c.bc_x = p.bc_x;
+    c.bc_y = p.bc_y;
+    c.plane = h->lay.plane;
+}
+
+}  // namespace dbm

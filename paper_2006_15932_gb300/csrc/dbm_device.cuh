@@ -1,0 +1,117 @@
+// dbm_device.cuh -- device building blocks of the D2V16 DBM step:
+// the equilibrium moments f-hat, the minmod limiter of the NND scheme and
+// the ghost-image bookkeeping of the boundary conditions.
+#pragma once
+
+#include "dbm_internal.h"
+
+namespace dbm {
+
+// f-hat_1..16 of the moment relations (section "Discrete Boltzmann model",
+// the f-hat list restating Eqs. relation1..relation7) at (n, u, theta = T/m)
+// with dpi = D + I.  Factored for the GPU; the same polynomials as printed.
+template <typename real>
+__device__ __forceinline__ void fhat16(real n, real ux, real uy, real th, real dpi, real fh[Q])
+{
+    const real u2 = ux * ux + uy * uy;
+    const real a2 = (dpi + real(2)) * th + u2;  // (D+I+2) T/m + u.u
+    const real a4 = (dpi + real(4)) * th + u2;  // (D+I+4) T/m + u.u
+    const real nux = n * ux, nuy = n * uy;
+    const real xx = ux * ux, yy = uy * uy;
+    fh[0] = n;
+    fh[1] = nux;
+    fh[2] = nuy;
+    fh[3] = n * (dpi * th + u2);
+    fh[4] = n * (th + xx);
+    fh[5] = nux * uy;
+    fh[6] = n * (th + yy);
+    fh[7] = nux * a2;
+    fh[8] = nuy * a2;
+    fh[9] = nux * (real(3) * th + xx);
+    fh[10] = nuy * (th + xx);
+    fh[11] = nux * (th + yy);
+    fh[12] = nuy * (real(3) * th + yy);
+    fh[13] = n * (a2 * th + xx * a4);
+    fh[14] = nux * uy * a4;
+    fh[15] = n * (a2 * th + yy * a4);
+}
+
+// minmod(a, b): the argument of smaller magnitude when both have the same
+// sign, else 0 (limiter of the NND scheme).
+__device__ __forceinline__ double minmod(double a, double b)
+{
+    const double s = copysign(1.0, a);
+    return s * fmax(fmin(fabs(a), s * b), 0.0);
+}
+__device__ __forceinline__ float minmod(float a, float b)
+{
+    const float s = copysignf(1.0f, a);
+    return s * fmaxf(fminf(fabsf(a), s * b), 0.0f);
+}
+
+// NND flux difference along one axis for a velocity component of sign
+// `sgn` (+1 or -1): (H_{j+1/2} - H_{j-1/2}) / c, from f_{j-2..j+2}.
+//   c > 0: H_{j+1/2} = c [f_j + mm(f_j - f_{j-1}, f_{j+1} - f_j)/2]
+//   c < 0: H_{j+1/2} = c [f_{j+1} - mm(f_{j+1} - f_j, f_{j+2} - f_{j+1})/2]
+template <typename real>
+__device__ __forceinline__ real nnd_diff_pos(real fm2, real fm1, real f0, real fp1)
+{
+    const real d0 = fm1 - fm2, d1 = f0 - fm1, d2 = fp1 - f0;
+    return d1 + real(0.5) * (minmod(d1, d2) - minmod(d0, d1));
+}
+template <typename real>
+__device__ __forceinline__ real nnd_diff_neg(real fm1, real f0, real fp1, real fp2)
+{
+    const real d1 = f0 - fm1, d2 = fp1 - f0, d3 = fp2 - fp1;
+    return d2 - real(0.5) * (minmod(d2, d3) - minmod(d1, d2));
+}
+
+// Ghost images of interior index k along an axis of n cells: the ghost
+// indices g in {-2, -1, n, n+1} whose source cell is k (periodic wrap, or
+// the edge cell for outflow).  Returns the count (0..4) and the indices.
+__device__ __forceinline__ int ghost_images(int k, int n, int bc, int g[4])
+{
+    int cnt = 0;
+    const int cand[4] = {-2, -1, n, n + 1};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = cand[j];
+        int src;
+        if (bc == DBM_BC_PERIODIC)
+            src = ((c % n) + n) % n;
+        else
+            src = c < 0 ? 0 : n - 1;
+        if (src == k) g[cnt++] = c;
+    }
+    return cnt;
+}
+
+struct Images {
+    int gx[4], gy[4];
+    int ngx, ngy;
+};
+
+__device__ __forceinline__ Images cell_images(int x, int y, int nx, int ny, int bc_x, int bc_y)
+{
+    Images im;
+    im.ngx = ghost_images(x, nx, bc_x, im.gx);
+    im.ngy = ghost_images(y, ny, bc_y, im.gy);
+    return im;
+}
+
+// Store v at interior cell (x, y) of plane base `pl` and at its ghost images.
+template <typename T>
+__device__ __forceinline__ void store_with_images(T *pl, long long cell, int x, int y, int pitch,
+                                                  const Images &im, T v)
+{
+    pl[cell] = v;
+    for (int j = 0; j < im.ngx; ++j) pl[(long long)(y + GY) * pitch + (im.gx[j] + GX)] = v;
+    for (int j = 0; j < im.ngy; ++j) pl[(long long)(im.gy[j] + GY) * pitch + (x + GX)] = v;
+}
+
+__device__ __forceinline__ void raise_flag(unsigned *flag, unsigned bits)
+{
+    if (bits) atomicOr(flag, bits);
+}
+
+}  // namespace dbm

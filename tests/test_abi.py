@@ -1,0 +1,144 @@
+"""The C-ABI library loads on the CPU host, exports every entry point of
+include/dbm.h, and its host-side validation (dbm_init, no GPU involved)
+accepts and rejects parameters as documented."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2006_15932_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_2006_15932_gb300 import build as B
+    from paper_2006_15932_gb300 import dbm
+
+    B.build()
+    dbm.load()
+    return dbm
+
+
+def _declared_functions():
+    txt = open(os.path.join(ROOT, "include", "dbm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dbm_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("dbm_init", "dbm_step", "dbm_moments", "dbm_nonequilibrium", "dbm_set_state",
+                     "dbm_conservation", "dbm_status", "dbm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(D):
+    import ctypes
+
+    lib = ctypes.CDLL(D.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    assert set(_declared_functions()) <= set(D.EXPORTS) | set()
+
+
+def _params(D, **over):
+    pb = W.random_smooth(16, 8, 2)
+    for k, v in over.items():
+        setattr(pb, k, v)
+    return D.params_from_problem(pb, "fp32")
+
+
+def test_init_accepts_a_valid_problem(D):
+    h = D.dbm_init(_params(D))
+    lay = D.dbm_get_layout(h)
+    assert lay.pitch % 32 == 0 and lay.pitch >= 16 + 4 + 2
+    assert lay.rows == 8 + 4 and lay.gx == 4 and lay.gy == 2
+    assert D.dbm_state_bytes(h) == 2 * 16 * lay.plane * 4
+    assert D.dbm_scratch_bytes(h) >= 256
+    assert D.dbm_steps_taken(h) == 0
+    D.dbm_destroy(h)
+
+
+def test_layout_per_precision(D):
+    pb = W.random_smooth(100, 7, 3)
+    for prec, eb in (("fp64", 8), ("fp32", 4)):
+        h = D.dbm_init(D.params_from_problem(pb, prec))
+        lay = D.dbm_get_layout(h)
+        assert lay.elem_bytes == eb
+        assert lay.bytes == 3 * 16 * lay.plane * eb
+        D.dbm_destroy(h)
+
+
+@pytest.mark.parametrize("case,code", [
+    (dict(nx=0), -1),
+    (dict(dt=-1.0), -1),
+    (dict(dt=1e-3), -7),           # CFL
+    (dict(bc_x=5), -1),
+])
+def test_init_rejects(D, case, code):
+    with pytest.raises(D.DbmError) as e:
+        D.dbm_init(_params(D, **case))
+    assert e.value.code == code
+    assert len(str(e.value)) > 20
+
+
+def test_init_rejects_bad_species(D):
+    pb = W.random_smooth(8, 8, 2)
+    pb.species[1].eta = (0.0, 0.0, 0.0, 0.0)  # singular moment matrix
+    with pytest.raises(D.DbmError) as e:
+        D.dbm_init(D.params_from_problem(pb))
+    assert e.value.code == -2
+    pb = W.random_smooth(8, 8, 2)
+    pb.species[0].tau = 0.0
+    with pytest.raises(D.DbmError):
+        D.dbm_init(D.params_from_problem(pb))
+    pb = W.random_smooth(8, 8, 2)
+    pb.species[0].tau = 4e-6  # dt >= 2 tau
+    with pytest.raises(D.DbmError) as e:
+        D.dbm_init(D.params_from_problem(pb))
+    assert e.value.code == -7
+    pb = W.random_smooth(8, 8, 9 - 1)
+    pb.species.append(pb.species[0])  # 9 species
+    with pytest.raises(ValueError):
+        D.params_from_problem(pb)
+
+
+def test_init_rejects_mass_creating_reaction(D):
+    pb = W.random_smooth(8, 8, 3, reactive=True)
+    h = D.dbm_init(D.params_from_problem(pb))
+    D.dbm_destroy(h)
+    pb.species[2].a = 1.5  # sum a m != 0
+    with pytest.raises(D.DbmError) as e:
+        D.dbm_init(D.params_from_problem(pb))
+    assert "conserve mass" in str(e.value)
+    pb = W.random_smooth(8, 8, 3, reactive=True)
+    pb.fuel = 7
+    with pytest.raises(D.DbmError):
+        D.dbm_init(D.params_from_problem(pb))
+
+
+def test_condition_check_is_unit_independent(D):
+    """The same velocity set in other velocity units (v and eta scaled by
+    300) is accepted: the check uses the row-equilibrated matrix."""
+    pb = W.random_smooth(8, 8, 1)
+    sp = pb.species[0]
+    sp.v = tuple(300 * x for x in sp.v)
+    sp.eta = tuple(300 * x for x in sp.eta)
+    pb.dt = 1e-8
+    pb.species[0].tau = 2e-8
+    h = D.dbm_init(D.params_from_problem(pb))
+    D.dbm_destroy(h)
+
+
+def test_calls_without_buffers_fail_cleanly(D):
+    h = D.dbm_init(_params(D))
+    with pytest.raises(D.DbmError) as e:
+        D.dbm_step(h, 1, 0)
+    assert e.value.code == -3
+    with pytest.raises(D.DbmError):
+        D.dbm_bind(h, 0, 0, 0)
+    D.dbm_destroy(h)
+    D.dbm_destroy(None)

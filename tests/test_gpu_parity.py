@@ -1,0 +1,247 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative L-inf = max|a - b| / max|b| per field):
+  FP64: 1e-12 on f and on every output field.
+  FP32: derived from float rounding: each step adds O(1e-7) relative
+        rounding to f; with the relaxation and the advection contracting,
+        the error grows at most linearly, so 50 steps stay below
+        1e-7 * 50 * (a safety factor of 4) = 2e-5 on f and the
+        conserved moments; the derived T and u have an extra factor of
+        cond ~ 10 from the subtraction E/n - u^2 (bound 2e-4).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2006_15932_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL_F = 2e-5
+
+
+def rel_linf(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_15932_gb300 import build as B
+    from paper_2006_15932_gb300 import dbm
+
+    B.build()
+    dbm.load()
+    return dbm
+
+
+def _oracle_f0(orc, pb):
+    p = W.to_oracle_params(pb)
+    return p, orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
+
+
+def _noneq_f(orc, pb, seed=3, rel=0.05):
+    """An oracle-built nonequilibrium state: f^eq of the problem's fields
+    times (1 + rel * noise), so that every term of the step is active."""
+    p, f0 = _oracle_f0(orc, pb)
+    rng = np.random.default_rng(seed)
+    return p, f0 * (1.0 + rel * rng.uniform(-1, 1, size=f0.shape))
+
+
+# ---------------------------------------------------------------------------
+# FP64: the configuration of the parity gate and random 2-D cases
+# ---------------------------------------------------------------------------
+
+def test_sod_tube_fp64_2000_steps(D, orc):
+    pb = W.sod_tube(400, 2000)
+    s = D.Solver(pb, "fp64")
+    s.set_state()
+    s.step(pb.nsteps)
+    f = s.get_f().cpu().numpy()
+    mom = s.moments().cpu().numpy()
+    assert s.status()[0] == 0
+    p, f0 = _oracle_f0(orc, pb)
+    fr, st = orc.run(p, f0, pb.nsteps)
+    assert st == 0
+    mr = orc.moments(p, fr)
+    assert rel_linf(f, fr) <= FP64_TOL
+    for k in range(mom.shape[0]):
+        assert rel_linf(mom[k], mr[k]) <= FP64_TOL, k
+
+
+@pytest.mark.parametrize("nx,ny,ns,bc,reactive,force", [
+    (37, 11, 3, (W.OUTFLOW, W.PERIODIC), True, True),
+    (33, 17, 2, (W.PERIODIC, W.PERIODIC), False, False),
+    (64, 9, 1, (W.PERIODIC, W.OUTFLOW), False, True),
+    (5, 40, 4, (W.OUTFLOW, W.OUTFLOW), True, False),
+])
+def test_random_fp64(D, orc, nx, ny, ns, bc, reactive, force):
+    pb = W.random_smooth(nx, ny, ns, seed=nx * ny, reactive=reactive, force=force, bc=bc)
+    p, f0 = _noneq_f(orc, pb)
+    s = D.Solver(pb, "fp64")
+    s.set_f(f0)
+    s.step(30)
+    f = s.get_f().cpu().numpy()
+    fr, st = orc.run(p, f0, 30)
+    assert st == 0 and s.status()[0] == 0
+    assert rel_linf(f, fr) <= FP64_TOL
+
+
+def test_set_state_matches_oracle_equilibrium(D, orc):
+    pb = W.random_smooth(29, 13, 3, seed=5)
+    s = D.Solver(pb, "fp64")
+    s.set_state()
+    p, f0 = _oracle_f0(orc, pb)
+    assert rel_linf(s.get_f().cpu().numpy(), f0) <= FP64_TOL
+
+
+def test_outputs_fp64(D, orc):
+    pb = W.random_smooth(31, 12, 3, seed=8, reactive=True)
+    p, f0 = _noneq_f(orc, pb, rel=0.1)
+    s = D.Solver(pb, "fp64")
+    s.set_f(f0)
+    mom = s.moments().cpu().numpy()
+    neq = s.nonequilibrium().cpu().numpy()
+    cons = s.conservation().cpu().numpy()
+    mr = orc.moments(p, f0)
+    nr = orc.nonequilibrium(p, f0)
+    cr = orc.conservation(p, f0)
+    for k in range(mr.shape[0]):
+        assert rel_linf(mom[k], mr[k]) <= FP64_TOL, ("moments", k)
+    for k in range(nr.shape[0]):
+        assert rel_linf(neq[k], nr[k]) <= 1e-11, ("noneq", k)
+    assert np.max(np.abs(cons - cr) / np.maximum(np.abs(cr), 1e-300)) <= 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,bc", [(1, 1, (W.PERIODIC, W.PERIODIC)), (1, 3, (W.OUTFLOW, W.PERIODIC)),
+                                      (2, 1, (W.PERIODIC, W.OUTFLOW)), (3, 2, (W.OUTFLOW, W.OUTFLOW))])
+def test_degenerate_grids(D, orc, nx, ny, bc):
+    pb = W.random_smooth(nx, ny, 2, seed=1, bc=bc)
+    p, f0 = _noneq_f(orc, pb)
+    s = D.Solver(pb, "fp64")
+    s.set_f(f0)
+    s.step(7)
+    fr, st = orc.run(p, f0, 7)
+    assert rel_linf(s.get_f().cpu().numpy(), fr) <= FP64_TOL
+
+
+def test_eight_species(D, orc):
+    pb = W.random_smooth(19, 6, 8, seed=2)
+    p, f0 = _noneq_f(orc, pb)
+    s = D.Solver(pb, "fp64")
+    s.set_f(f0)
+    s.step(5)
+    fr, _ = orc.run(p, f0, 5)
+    assert rel_linf(s.get_f().cpu().numpy(), fr) <= FP64_TOL
+
+
+def test_zero_steps_is_identity(D, orc):
+    pb = W.random_smooth(10, 4, 2, seed=4)
+    p, f0 = _noneq_f(orc, pb)
+    s = D.Solver(pb, "fp64")
+    s.set_f(f0)
+    s.step(0)
+    assert np.array_equal(s.get_f().cpu().numpy(), f0)
+
+
+def test_checkpoint_resume_is_bitwise(D, orc):
+    pb = W.random_smooth(21, 9, 2, seed=6, reactive=False)
+    for prec in ("fp64", "fp32"):
+        a = D.Solver(pb, prec)
+        a.set_state()
+        a.step(10)
+        a.step(10)
+        fa = a.get_f().cpu().numpy()
+        b = D.Solver(pb, prec)
+        b.set_state()
+        b.step(10)
+        ck = b.get_f()
+        c = D.Solver(pb, prec)
+        c.set_f(ck)
+        c.step(10)
+        assert np.array_equal(c.get_f().cpu().numpy(), fa)
+
+
+def test_health_flag_reports_negative_density(D, orc):
+    pb = W.random_smooth(8, 8, 2, seed=9)
+    p, f0 = _oracle_f0(orc, pb)
+    f0[1, :, 3, 4] *= -1.0  # the host plants a negative density at one cell
+    s = D.Solver(pb, "fp64")
+    s.set_f(f0)
+    s.step(1)
+    rc, bits = s.status()
+    assert rc == -6 and bits & 1
+    s.set_state()  # a fresh state clears the flag
+    s.step(1)
+    assert s.status() == (0, 0)
+
+
+# ---------------------------------------------------------------------------
+# FP32
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("reactive", [False, True])
+def test_fp32_against_oracle(D, orc, reactive):
+    pb = W.random_smooth(70, 23, 3, seed=12, reactive=reactive, bc=(W.OUTFLOW, W.PERIODIC))
+    p, f0 = _noneq_f(orc, pb)
+    s = D.Solver(pb, "fp32")
+    s.set_f(f0)
+    s.step(50)
+    f = s.get_f().cpu().numpy()
+    mom = s.moments().cpu().numpy()
+    fr, _ = orc.run(p, f0, 50)
+    mr = orc.moments(p, fr)
+    assert rel_linf(f, fr) <= FP32_TOL_F
+    for k in range(mr.shape[0]):
+        tol = 2e-4 if (k % 4 in (1, 2, 3) or k >= 4 * 3) else FP32_TOL_F
+        assert rel_linf(mom[k], mr[k]) <= tol, k
+
+
+def test_fp32_conservation_drift(D, orc):
+    pb = W.random_smooth(64, 64, 2, seed=13)
+    s = D.Solver(pb, "fp32")
+    s.set_state()
+    c0 = s.conservation().cpu().numpy()
+    s.step(200)
+    c1 = s.conservation().cpu().numpy()
+    assert np.max(np.abs(c1[:2] - c0[:2]) / np.abs(c0[:2])) < 1e-6
+    assert abs(c1[4] - c0[4]) / abs(c0[4]) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads: sampled windows of one step at the bench sizes
+# ---------------------------------------------------------------------------
+
+def _windows(nx, ny, rng, k=4, w=24):
+    out = [(0, min(w, nx), 0, min(w, ny)), (max(0, nx - w), nx, max(0, ny - w), ny)]
+    for _ in range(k):
+        x0 = int(rng.integers(0, max(1, nx - w)))
+        y0 = int(rng.integers(0, max(1, ny - w)))
+        out.append((x0, min(nx, x0 + w), y0, min(ny, y0 + w)))
+    return out
+
+
+@pytest.mark.parametrize("which", ["kh4096", "reactive1024"])
+def test_full_size_one_step_sampled(D, orc, which):
+    pb = W.kh_shear_layer(4096) if which == "kh4096" else W.reactive_premixed()
+    s = D.Solver(pb, "fp32")
+    s.set_state()
+    f0 = s.get_f()
+    s.step(1)
+    f1 = s.get_f()
+    assert s.status()[0] == 0
+    p = W.to_oracle_params(pb)
+    f0n = f0.cpu().numpy()
+    f1n = f1.cpu().numpy()
+    del f0, f1
+    rng = np.random.default_rng(0)
+    for (x0, x1, y0, y1) in _windows(pb.nx, pb.ny, rng):
+        want, st = orc.step_region(p, f0n, x0, x1, y0, y1)
+        got = f1n[:, :, y0:y1, x0:x1]
+        assert rel_linf(got, want) <= 1e-6, (x0, y0)
