@@ -60,13 +60,13 @@ enum dbm_status_code {
     DBM_ERR_UNBOUND = -3,     /* state buffers not bound yet                   */
     DBM_ERR_CUDA = -4,        /* a CUDA runtime call or launch failed           */
     DBM_ERR_NONFINITE = -5,   /* device health flag: a non-finite moment        */
-    DBM_ERR_NEGATIVE = -6,    /* device health flag: n^s <= 0, T <= 0 or n* < 0 */
+    DBM_ERR_NEGATIVE = -6,    /* device health flag: negative density, T <= 0 or n* < 0 */
     DBM_ERR_STABILITY = -7    /* CFL or dt/tau stability limit exceeded         */
 };
 
 /* Health-flag bits as kept on the device (dbm_status_bits). */
 enum dbm_health_bits {
-    DBM_HEALTH_DENSITY = 1,      /* n^s <= 0 or not finite      */
+    DBM_HEALTH_DENSITY = 1,      /* n^s < -1e-6 sum|n^s|, no matter at all, or not finite */
     DBM_HEALTH_TEMPERATURE = 2,  /* mixture T <= 0 or not finite */
     DBM_HEALTH_NSTAR = 4,        /* n^s* < 0 after the reaction  */
     DBM_HEALTH_NONFINITE = 8     /* a non-finite moment           */
@@ -128,6 +128,13 @@ int dbm_init(const dbm_params *params, dbm_handle **out);
  * successful one). */
 const char *dbm_init_error(void);
 
+/* The equilibrium matrix M^-1 of one species as used by the kernels,
+ * out[16*16] row-major (row i = velocity, column k = moment f-hat_k), so
+ * that f^eq_i = sum_k out[16 i + k] f-hat_k (section "Discrete Boltzmann
+ * model").  It is the inverse of the double matrix M rounded correctly to
+ * double (LU, then refinement with compensated residuals).  Host only. */
+int dbm_equilibrium_matrix(const dbm_handle *h, int species, double *out);
+
 /* Storage geometry and size of one state buffer for this handle. */
 int dbm_get_layout(const dbm_handle *h, dbm_layout *out);
 
@@ -161,7 +168,8 @@ int dbm_get_f(dbm_handle *h, double *f, void *stream);
 int dbm_step(dbm_handle *h, int nsteps, void *stream);
 
 /* Macroscopic fields of the current state, FP64 out[(4S+5)][ny][nx]:
- *   rows 4s..4s+3: n^s, u^s_x, u^s_y, T^s = m^s (E^s/n^s - u^s.u^s)/(D+I^s);
+ *   rows 4s..4s+3: n^s, u^s_x, u^s_y, T^s = m^s (E^s/n^s - u^s.u^s)/(D+I^s)
+ *   (u^s = T^s = 0 for an absent species, n^s = 0);
  *   rows 4S..4S+4: rho = sum m^s n^s, u_x, u_y, T (mixture, from conservation
  *   of the collision term), p = n T with n = sum n^s.  Async on stream. */
 int dbm_moments(dbm_handle *h, double *out, void *stream);

@@ -21,8 +21,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdbm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code without contraction: the moment matrix and its inverse are built
+# with the same IEEE operations on every host architecture
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "-I", INCLUDE, "-I", CSRC]
+              "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:

@@ -96,6 +96,45 @@ static int lu_inverse(const double A[Q][Q], double Ainv[Q][Q])
     return 0;
 }
 
+// Compensated dot product c - sum_k a[k] b[k*stride] (Ogita-Rump-Oishi
+// "Dot2": error-free products via fma and error-free sums), as accurate as
+// if accumulated in twice the working precision.
+static double residual_dot2(double c, const double *a, const double *b, int stride)
+{
+    double s = c, err = 0.0;
+    for (int k = 0; k < Q; ++k) {
+        const double p = -a[k] * b[k * stride];
+        const double pe = fma(-a[k], b[k * stride], -p);
+        const double t = s + p;
+        const double z = t - s;
+        err += ((s - (t - z)) + (p - z)) + pe;
+        s = t;
+    }
+    return s + err;
+}
+
+// Newton-Schulz style refinement X <- X + X (I - A X) with the residual
+// from residual_dot2: the error of X squares at each pass, so X becomes the
+// inverse of A rounded correctly to double (ties aside).  Exact conservation
+// by f^eq = M^-1 f-hat needs this: a few ulps of error in M^-1 bias the
+// mass, momentum and energy of every collision the same way, and that bias
+// accumulates step after step.
+static void refine_inverse(const double A[Q][Q], double X[Q][Q], int passes)
+{
+    for (int it = 0; it < passes; ++it) {
+        double R[Q][Q], Xn[Q][Q];
+        for (int r = 0; r < Q; ++r)
+            for (int c = 0; c < Q; ++c) R[r][c] = residual_dot2(r == c ? 1.0 : 0.0, A[r], &X[0][c], Q);
+        for (int r = 0; r < Q; ++r)
+            for (int c = 0; c < Q; ++c) {
+                double d = 0.0;
+                for (int k = 0; k < Q; ++k) d += X[r][k] * R[k][c];
+                Xn[r][c] = X[r][c] + d;
+            }
+        memcpy(X, Xn, sizeof(Xn));
+    }
+}
+
 static double norm_inf(const double A[Q][Q])
 {
     double best = 0.0;
@@ -211,6 +250,7 @@ int dbm_init(const dbm_params *params, dbm_handle **out)
                 rc = fail(h, DBM_ERR_SINGULAR, "species %d: moment matrix M is singular", s);
                 break;
             }
+            refine_inverse(M, Mi, 3);
             // condition number of the row-equilibrated matrix D M (D scales each
             // row to unit max-norm), independent of the unit of velocity
             double rowmax[Q], DM[Q][Q], MiD[Q][Q];
@@ -248,6 +288,13 @@ int dbm_init(const dbm_params *params, dbm_handle **out)
     g_init_error[0] = 0;
     compute_layout(h);
     *out = h;
+    return DBM_OK;
+}
+
+int dbm_equilibrium_matrix(const dbm_handle *h, int species, double *out)
+{
+    if (!h || !out || species < 0 || species >= h->p.nspecies) return DBM_ERR_INVALID;
+    memcpy(out, h->cinv[species], sizeof(h->cinv[species]));
     return DBM_OK;
 }
 

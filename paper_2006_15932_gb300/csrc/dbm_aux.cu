@@ -129,11 +129,14 @@ __global__ void __launch_bounds__(256)
     double rho = 0, ntot = 0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        const double usx = jx[s] / n[s], usy = jy[s] / n[s];
+        // an absent species (n = 0) reports zero velocity and temperature
+        const bool here = n[s] != 0.0;
+        const double usx = here ? jx[s] / n[s] : 0.0, usy = here ? jy[s] / n[s] : 0.0;
         out[(4 * s + 0) * N + d] = n[s];
         out[(4 * s + 1) * N + d] = usx;
         out[(4 * s + 2) * N + d] = usy;
-        out[(4 * s + 3) * N + d] = c.m[s] * (en[s] / n[s] - (usx * usx + usy * usy)) / c.dpi[s];
+        out[(4 * s + 3) * N + d] =
+            here ? c.m[s] * (en[s] / n[s] - (usx * usx + usy * usy)) / c.dpi[s] : 0.0;
         rho += c.m[s] * n[s];
         ntot += n[s];
     }

@@ -75,10 +75,16 @@ __global__ void __launch_bounds__(256)
     }
     const double Td = num / den;
 
+    // health: a species may be absent (n = 0) or slightly negative from
+    // numerical diffusion; flag densities below -1e-6 of the mixture
     unsigned bad = 0;
+    real nabs = 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) nabs += fabs(n[s]);
 #pragma unroll
     for (int s = 0; s < S; ++s)
-        if (!(n[s] > real(0))) bad |= DBM_HEALTH_DENSITY;
+        if (!(n[s] >= real(-1e-6) * nabs)) bad |= DBM_HEALTH_DENSITY;
+    if (!(nabs > real(0))) bad |= DBM_HEALTH_DENSITY;
     if (!(Td > 0.0)) bad |= DBM_HEALTH_TEMPERATURE;
     if (!isfinite(Td) || !isfinite((double)ux) || !isfinite((double)uy)) bad |= DBM_HEALTH_NONFINITE;
 
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(256)
         }
         const real inv_m = real(1) / c.m[s];
         fhat16<real>(ns, ux, uy, (real)Ts * inv_m, c.dpi[s], fh);
-        if (c.has_force) {
+        if (c.has_force && n[s] != real(0)) {  // an absent species feels no force
             const real usx = jx[s] / n[s], usy = jy[s] / n[s];
             const real ths = (en[s] / n[s] - (usx * usx + usy * usy)) / c.dpi[s];
             real g1[Q], g0[Q];

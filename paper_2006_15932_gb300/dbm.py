@@ -34,7 +34,7 @@ ERRORS = {
     -7: "DBM_ERR_STABILITY",
 }
 EXPORTS = [
-    "dbm_init", "dbm_init_error", "dbm_get_layout", "dbm_state_bytes", "dbm_scratch_bytes",
+    "dbm_init", "dbm_init_error", "dbm_equilibrium_matrix", "dbm_get_layout", "dbm_state_bytes", "dbm_scratch_bytes",
     "dbm_bind", "dbm_set_state", "dbm_set_f", "dbm_get_f", "dbm_step", "dbm_moments",
     "dbm_nonequilibrium", "dbm_conservation", "dbm_status", "dbm_steps_taken",
     "dbm_last_error", "dbm_destroy",
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
     vp = C.c_void_p
     L.dbm_init.argtypes = [C.POINTER(dbm_params), C.POINTER(H)]
     L.dbm_init_error.restype = C.c_char_p
+    L.dbm_equilibrium_matrix.argtypes = [H, C.c_int, vp]
     L.dbm_get_layout.argtypes = [H, C.POINTER(dbm_layout)]
     L.dbm_state_bytes.argtypes = [H, C.POINTER(C.c_size_t)]
     L.dbm_scratch_bytes.argtypes = [H, C.POINTER(C.c_size_t)]
@@ -176,6 +177,12 @@ def dbm_init(params: dbm_params) -> int:
     if rc != OK:
         raise DbmError(rc, L.dbm_init_error().decode())
     return h.value
+
+
+def dbm_equilibrium_matrix(h, species: int) -> np.ndarray:
+    out = np.zeros((Q, Q))
+    _check(h, load().dbm_equilibrium_matrix(h, int(species), out.ctypes.data))
+    return out
 
 
 def dbm_get_layout(h) -> dbm_layout:

@@ -142,3 +142,38 @@ def test_calls_without_buffers_fail_cleanly(D):
         D.dbm_bind(h, 0, 0, 0)
     D.dbm_destroy(h)
     D.dbm_destroy(None)
+
+
+def test_equilibrium_matrix_is_correctly_rounded(D):
+    """The library's M^-1 (host FP64, its own LU and refinement) equals the
+    exact rational inverse of M rounded to double in every nonzero entry,
+    like the oracle's: the two sides then share the same equilibrium
+    operator without sharing code."""
+    from tests.test_oracle_pins import _exact_inverse
+
+    pb = W.random_smooth(8, 8, 3)
+    h = D.dbm_init(D.params_from_problem(pb))
+    try:
+        for s, sp in enumerate(pb.species):
+            Mi = D.dbm_equilibrium_matrix(h, s)
+            # M rebuilt here from the velocity set, row k = moment monomial k
+            M = _moment_matrix_from_velocities(sp)
+            E = _exact_inverse(M)
+            nz = E != 0
+            assert np.array_equal(Mi[nz], E[nz])
+            assert np.max(np.abs(Mi[~nz])) <= 1e-30 * np.max(np.abs(E))
+    finally:
+        D.dbm_destroy(h)
+
+
+def _moment_matrix_from_velocities(sp):
+    dirs = [(1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    M = np.zeros((16, 16))
+    for i in range(16):
+        r = i // 4
+        dx, dy = dirs[(4 if r % 2 else 0) + i % 4]
+        x, y = dx * sp.v[r], dy * sp.v[r]
+        q = x * x + y * y + sp.eta[r] * sp.eta[r]
+        M[:, i] = [1.0, x, y, q, x * x, x * y, y * y, q * x, q * y, x * x * x, x * x * y, x * y * y,
+                   y * y * y, q * x * x, q * x * y, q * y * y]
+    return M

@@ -127,6 +127,40 @@ def test_inverse_matches_library(orc):
         assert np.max(np.abs(M @ Mi - np.eye(16))) < 1e-11
 
 
+def _exact_inverse(M):
+    """Gauss-Jordan on exact rationals (every double is a rational), then
+    each entry rounded to the nearest double by float(Fraction)."""
+    from fractions import Fraction
+
+    n = M.shape[0]
+    A = [[Fraction(float(M[r, c])) for c in range(n)] + [Fraction(int(r == c)) for c in range(n)]
+         for r in range(n)]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        p = A[col][col]
+        A[col] = [x / p for x in A[col]]
+        for r in range(n):
+            if r != col and A[r][col] != 0:
+                fac = A[r][col]
+                A[r] = [a - fac * b for a, b in zip(A[r], A[col])]
+    return np.array([[float(A[r][n + c]) for c in range(n)] for r in range(n)])
+
+
+def test_minv_is_the_correctly_rounded_exact_inverse(orc):
+    """f^eq = M^-1 f-hat with M^-1 rounded correctly from the exact inverse
+    of M: every nonzero entry equals the exact rational inverse rounded to
+    double; the structural zeros of the D2V16 symmetry stay below 1e-30 of
+    the largest entry."""
+    for sp in _species_list(orc, 3):
+        E = _exact_inverse(orc.moment_matrix(sp))
+        Mi = orc.minv(orc.Params(nx=1, ny=1, species=[sp]))[0]
+        nz = E != 0
+        assert np.array_equal(Mi[nz], E[nz])
+        assert np.max(np.abs(Mi[~nz])) <= 1e-30 * np.max(np.abs(E))
+        assert nz.sum() == 208
+
+
 def test_all_eta_zero_is_singular(orc):
     sp = orc.Species(eta=(0.0, 0.0, 0.0, 0.0))
     M = orc.moment_matrix(sp)
