@@ -181,14 +181,17 @@ def cpu_baseline(pb_full, precision, seconds):
                    T=pb_full.T[y0:y0 + ny, x0:x0 + nx])
     p = W.to_oracle_params(pb)
     f = O.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
+    O.run(p, f, 1)  # start the OpenMP thread pool
     t0 = time.perf_counter()
-    f, _ = O.run(p, f, 1)
+    f, st = O.run(p, f, 1)
     t1 = time.perf_counter()
     per_step = max(t1 - t0, 1e-6)
-    steps = max(1, min(200, int(seconds / per_step)))
+    steps = max(1, min(1000, int(seconds / per_step)))
     t0 = time.perf_counter()
-    O.run(p, f, steps)
+    _, st2 = O.run(p, f, steps)
     dt = time.perf_counter() - t0
+    if st or st2:
+        raise RuntimeError(f"oracle status {st}/{st2} on the CPU-baseline sample: the timing would be cut short")
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": nx * ny * pb.ns * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{nx}x{ny} window of the {pb_full.nx}x{pb_full.ny} grid, {pb.ns} species, "

@@ -402,7 +402,7 @@ int orc_cell_rhs(const orc_params *p, const double *Minv, const double *fc, doub
         /* Eq. ReactionTerm: f^eq(n^s*, u, T*) with reading R2 */
         const double nstar = n[s] + tau * sp->a * omega;
         const double Tstar = T + tau * dTdt;
-        if (nstar < 0.0) st |= ORC_NEGATIVE_NSTAR;
+        if (p->k_ov != 0.0 && nstar < -1e-6 * ntot) st |= ORC_NEGATIVE_NSTAR;
         double feq_r[ORC_Q];
         orc_feq(Mi, nstar, Ux, Uy, Tstar, sp->m, sp->I, feq_r);
         /* Eq. ForceTerm with reading R3: u^dag = u^s + a tau, T^dag = T^s */

@@ -46,63 +46,63 @@ static void build_moment_matrix(const dbm_species &sp, double M[Q][Q])
     }
 }
 
-// LU factorisation with partial pivoting (Doolittle, in place), then
-// M^-1 column by column from forward and back substitution.
-// Returns 0, or -1 when a pivot vanishes.
-static int lu_inverse(const double A[Q][Q], double Ainv[Q][Q])
+// LU factorisation with partial pivoting (Doolittle, in place) of the
+// n x n row-major A, then A^-1 column by column from forward and back
+// substitution.  Returns 0, or -1 when a pivot vanishes.
+static int lu_inverse_n(const double *A, double *Ainv, int n)
 {
-    double LU[Q][Q];
+    double LU[Q * Q];
     int perm[Q];
-    memcpy(LU, A, sizeof(LU));
-    for (int i = 0; i < Q; ++i) perm[i] = i;
-    for (int k = 0; k < Q; ++k) {
+    memcpy(LU, A, sizeof(double) * n * n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int k = 0; k < n; ++k) {
         int piv = k;
-        double best = fabs(LU[k][k]);
-        for (int r = k + 1; r < Q; ++r)
-            if (fabs(LU[r][k]) > best) {
-                best = fabs(LU[r][k]);
+        double best = fabs(LU[k * n + k]);
+        for (int r = k + 1; r < n; ++r)
+            if (fabs(LU[r * n + k]) > best) {
+                best = fabs(LU[r * n + k]);
                 piv = r;
             }
         if (best == 0.0) return -1;
         if (piv != k) {
-            for (int c = 0; c < Q; ++c) {
-                const double t = LU[k][c];
-                LU[k][c] = LU[piv][c];
-                LU[piv][c] = t;
+            for (int c = 0; c < n; ++c) {
+                const double t = LU[k * n + c];
+                LU[k * n + c] = LU[piv * n + c];
+                LU[piv * n + c] = t;
             }
             const int t = perm[k];
             perm[k] = perm[piv];
             perm[piv] = t;
         }
-        for (int r = k + 1; r < Q; ++r) {
-            LU[r][k] /= LU[k][k];
-            const double l = LU[r][k];
-            for (int c = k + 1; c < Q; ++c) LU[r][c] -= l * LU[k][c];
+        for (int r = k + 1; r < n; ++r) {
+            LU[r * n + k] /= LU[k * n + k];
+            const double l = LU[r * n + k];
+            for (int c = k + 1; c < n; ++c) LU[r * n + c] -= l * LU[k * n + c];
         }
     }
-    for (int col = 0; col < Q; ++col) {
+    for (int col = 0; col < n; ++col) {
         double z[Q];
-        for (int r = 0; r < Q; ++r) {  // L z = P e_col
+        for (int r = 0; r < n; ++r) {  // L z = P e_col
             double s = (perm[r] == col) ? 1.0 : 0.0;
-            for (int c = 0; c < r; ++c) s -= LU[r][c] * z[c];
+            for (int c = 0; c < r; ++c) s -= LU[r * n + c] * z[c];
             z[r] = s;
         }
-        for (int r = Q - 1; r >= 0; --r) {  // U x = z
+        for (int r = n - 1; r >= 0; --r) {  // U x = z
             double s = z[r];
-            for (int c = r + 1; c < Q; ++c) s -= LU[r][c] * Ainv[c][col];
-            Ainv[r][col] = s / LU[r][r];
+            for (int c = r + 1; c < n; ++c) s -= LU[r * n + c] * Ainv[c * n + col];
+            Ainv[r * n + col] = s / LU[r * n + r];
         }
     }
     return 0;
 }
 
-// Compensated dot product c - sum_k a[k] b[k*stride] (Ogita-Rump-Oishi
+// Compensated dot product c - sum_k a[k] b[k*stride], k < n (Ogita-Rump-Oishi
 // "Dot2": error-free products via fma and error-free sums), as accurate as
 // if accumulated in twice the working precision.
-static double residual_dot2(double c, const double *a, const double *b, int stride)
+static double residual_dot2(double c, const double *a, const double *b, int stride, int n)
 {
     double s = c, err = 0.0;
-    for (int k = 0; k < Q; ++k) {
+    for (int k = 0; k < n; ++k) {
         const double p = -a[k] * b[k * stride];
         const double pe = fma(-a[k], b[k * stride], -p);
         const double t = s + p;
@@ -113,25 +113,123 @@ static double residual_dot2(double c, const double *a, const double *b, int stri
     return s + err;
 }
 
-// Newton-Schulz style refinement X <- X + X (I - A X) with the residual
-// from residual_dot2: the error of X squares at each pass, so X becomes the
-// inverse of A rounded correctly to double (ties aside).  Exact conservation
-// by f^eq = M^-1 f-hat needs this: a few ulps of error in M^-1 bias the
-// mass, momentum and energy of every collision the same way, and that bias
+// Refinement X <- X + X (I - A X) with the residual from residual_dot2:
+// the error of X squares at each pass, so X becomes the inverse of A
+// rounded correctly to double (ties aside).  Exact conservation by
+// f^eq = M^-1 f-hat needs this: a few ulps of error in M^-1 bias the mass,
+// momentum and energy of every collision the same way, and that bias
 // accumulates step after step.
-static void refine_inverse(const double A[Q][Q], double X[Q][Q], int passes)
+static void refine_inverse_n(const double *A, double *X, int n, int passes)
 {
     for (int it = 0; it < passes; ++it) {
-        double R[Q][Q], Xn[Q][Q];
-        for (int r = 0; r < Q; ++r)
-            for (int c = 0; c < Q; ++c) R[r][c] = residual_dot2(r == c ? 1.0 : 0.0, A[r], &X[0][c], Q);
-        for (int r = 0; r < Q; ++r)
-            for (int c = 0; c < Q; ++c) {
+        double R[Q * Q], Xn[Q * Q];
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < n; ++c)
+                R[r * n + c] = residual_dot2(r == c ? 1.0 : 0.0, A + r * n, X + c, n, n);
+        for (int r = 0; r < n; ++r)
+            for (int c = 0; c < n; ++c) {
                 double d = 0.0;
-                for (int k = 0; k < Q; ++k) d += X[r][k] * R[k][c];
-                Xn[r][c] = X[r][c] + d;
+                for (int k = 0; k < n; ++k) d += X[r * n + k] * R[k * n + c];
+                Xn[r * n + c] = X[r * n + c] + d;
             }
-        memcpy(X, Xn, sizeof(Xn));
+        memcpy(X, Xn, sizeof(double) * n * n);
+    }
+}
+
+static int inverse_refined(const double *A, double *X, int n)
+{
+    if (lu_inverse_n(A, X, n) != 0) return -1;
+    refine_inverse_n(A, X, n, 3);
+    return 0;
+}
+
+// The symmetry blocks of M (see dbm_step_impl.cuh): with ring means A_r,
+// axis quadrupoles B_a, B_c, diagonal quadrupoles H_b, H_d and vector parts
+// (E on axis rings, G on diagonal rings) as unknowns, the moment relations
+// read
+//   (f1, f4, f5+f7, f14+f16) = bA (A_a, A_b, A_c, A_d)
+//   (f5-f7, f14-f16)         = bB (B_a, B_c)
+//   (f6, f15)                = bH (H_b, H_d)
+//   (f2, f8, f10, f12)       = bX (E_xa, G_xb, E_xc, G_xd)   (and y alike)
+// with entries from the ring sums of the monomials (4 velocities per ring;
+// |v|^2 = v^2 on axis rings and 2 v^2 on diagonal rings).
+static int symmetry_blocks(const dbm_species &sp, double iA[16], double iB[4], double iH[4],
+                           double iX[16])
+{
+    double v[4], q[4], w[4];
+    for (int r = 0; r < 4; ++r) {
+        v[r] = sp.v[r];
+        const double v2 = v[r] * v[r] * ((r & 1) ? 2.0 : 1.0);
+        q[r] = v2 + sp.eta[r] * sp.eta[r];
+        w[r] = (r & 1) ? 4.0 : 2.0;  // weight of the vector part in a ring sum
+    }
+    double bA[16], bB[4], bH[4], bX[16];
+    for (int r = 0; r < 4; ++r) {
+        const double g = (r & 1) ? 8.0 : 4.0;  // sum over the ring of v_x^2 + v_y^2 per unit v^2
+        bA[0 * 4 + r] = 4.0;
+        bA[1 * 4 + r] = 4.0 * q[r];
+        bA[2 * 4 + r] = g * v[r] * v[r];
+        bA[3 * 4 + r] = g * q[r] * v[r] * v[r];
+        bX[0 * 4 + r] = w[r] * v[r];
+        bX[1 * 4 + r] = w[r] * q[r] * v[r];
+        bX[2 * 4 + r] = w[r] * v[r] * v[r] * v[r];
+        bX[3 * 4 + r] = (r & 1) ? 4.0 * v[r] * v[r] * v[r] : 0.0;
+    }
+    for (int j = 0; j < 2; ++j) {
+        const int ra = 2 * j, rb = 2 * j + 1;
+        bB[0 * 2 + j] = 4.0 * v[ra] * v[ra];
+        bB[1 * 2 + j] = 4.0 * q[ra] * v[ra] * v[ra];
+        bH[0 * 2 + j] = 4.0 * v[rb] * v[rb];
+        bH[1 * 2 + j] = 4.0 * q[rb] * v[rb] * v[rb];
+    }
+    if (inverse_refined(bA, iA, 4) || inverse_refined(bB, iB, 2) || inverse_refined(bH, iH, 2) ||
+        inverse_refined(bX, iX, 4))
+        return -1;
+    return 0;
+}
+
+// f^eq of all 16 velocities from the blocks, for unit moment vectors:
+// column k of the matrix the kernels apply, to compare with M^-1.
+static void blocks_to_matrix(const double iA[16], const double iB[4], const double iH[4],
+                             const double iX[16], double out[Q][Q])
+{
+    for (int k = 0; k < Q; ++k) {
+        double fh[Q] = {0};
+        fh[k] = 1.0;
+        const double cA[4] = {fh[0], fh[3], fh[4] + fh[6], fh[13] + fh[15]};
+        const double cB[2] = {fh[4] - fh[6], fh[13] - fh[15]};
+        const double cH[2] = {fh[5], fh[14]};
+        const double cX[4] = {fh[1], fh[7], fh[9], fh[11]};
+        const double cY[4] = {fh[2], fh[8], fh[12], fh[10]};
+        double A[4], B[2], H[2], X[4], Y[4];
+        for (int r = 0; r < 4; ++r) {
+            A[r] = X[r] = Y[r] = 0.0;
+            for (int j = 0; j < 4; ++j) {
+                A[r] += iA[r * 4 + j] * cA[j];
+                X[r] += iX[r * 4 + j] * cX[j];
+                Y[r] += iX[r * 4 + j] * cY[j];
+            }
+        }
+        for (int r = 0; r < 2; ++r) {
+            B[r] = iB[r * 2] * cB[0] + iB[r * 2 + 1] * cB[1];
+            H[r] = iH[r * 2] * cH[0] + iH[r * 2 + 1] * cH[1];
+        }
+        for (int r = 0; r < 4; ++r) {
+            const int i = 4 * r;
+            if ((r & 1) == 0) {
+                const double b = B[r >> 1];
+                out[i + 0][k] = A[r] + X[r] + b;
+                out[i + 1][k] = A[r] + Y[r] - b;
+                out[i + 2][k] = A[r] - X[r] + b;
+                out[i + 3][k] = A[r] - Y[r] - b;
+            } else {
+                const double hq = H[r >> 1];
+                out[i + 0][k] = A[r] + X[r] + Y[r] + hq;
+                out[i + 1][k] = A[r] - X[r] + Y[r] - hq;
+                out[i + 2][k] = A[r] - X[r] - Y[r] + hq;
+                out[i + 3][k] = A[r] + X[r] - Y[r] - hq;
+            }
+        }
     }
 }
 
@@ -207,7 +305,7 @@ static void compute_layout(dbm_handle *h)
     memset(&L, 0, sizeof(L));
     L.gx = GX;
     L.gy = GY;
-    L.pitch = ((GX + p.nx + 2) + 31) / 32 * 32;
+    L.pitch = ((GX + p.nx + 4) + 31) / 32 * 32;  // room for the pair loads at x0+2, x0+3
     L.rows = p.ny + 2 * GY;
     L.plane = (long long)L.pitch * L.rows;
     const size_t nplanes = (size_t)p.nspecies * Q;
@@ -246,11 +344,10 @@ int dbm_init(const dbm_params *params, dbm_handle **out)
         for (int s = 0; s < h->p.nspecies && rc == DBM_OK; ++s) {
             double M[Q][Q], Mi[Q][Q];
             build_moment_matrix(h->p.sp[s], M);
-            if (lu_inverse(M, Mi) != 0) {
+            if (inverse_refined(&M[0][0], &Mi[0][0], Q) != 0) {
                 rc = fail(h, DBM_ERR_SINGULAR, "species %d: moment matrix M is singular", s);
                 break;
             }
-            refine_inverse(M, Mi, 3);
             // condition number of the row-equilibrated matrix D M (D scales each
             // row to unit max-norm), independent of the unit of velocity
             double rowmax[Q], DM[Q][Q], MiD[Q][Q];
@@ -278,6 +375,29 @@ int dbm_init(const dbm_params *params, dbm_handle **out)
                           "choose eta > 0 and distinct ring speeds",
                           s, cond, res);
             memcpy(h->cinv[s], Mi, sizeof(Mi));
+            if (rc != DBM_OK) break;
+            // symmetry blocks used by the step kernel; they must reproduce M^-1
+            double iA[16], iB[4], iH[4], iX[16], Mb[Q][Q];
+            if (symmetry_blocks(h->p.sp[s], iA, iB, iH, iX) != 0) {
+                rc = fail(h, DBM_ERR_SINGULAR, "species %d: a symmetry block of M is singular", s);
+                break;
+            }
+            blocks_to_matrix(iA, iB, iH, iX, Mb);
+            double dmax = 0.0, mmax = 0.0;
+            for (int r = 0; r < Q; ++r)
+                for (int c = 0; c < Q; ++c) {
+                    dmax = fmax(dmax, fabs(Mb[r][c] - Mi[r][c]));
+                    mmax = fmax(mmax, fabs(Mi[r][c]));
+                }
+            if (!(dmax <= 1e-13 * mmax)) {
+                rc = fail(h, DBM_ERR_SINGULAR, "species %d: symmetry blocks disagree with M^-1 (%g)", s,
+                          dmax / mmax);
+                break;
+            }
+            memcpy(h->eqA[s], iA, sizeof(iA));
+            memcpy(h->eqB[s], iB, sizeof(iB));
+            memcpy(h->eqH[s], iH, sizeof(iH));
+            memcpy(h->eqX[s], iX, sizeof(iX));
         }
     }
     if (rc != DBM_OK) {

@@ -21,33 +21,41 @@ void fill_step_consts(const dbm_handle *h, StepConsts<real, S> &c)
 {
     memset(&c, 0, sizeof(c));
     const dbm_params &p = h->p;
+    double src = 0.0;
     for (int s = 0; s < S; ++s) {
         const dbm_species &sp = p.sp[s];
-        for (int i = 0; i < Q; ++i)
-            for (int k = 0; k < Q; ++k) c.cinv[s][i][k] = (real)h->cinv[s][i][k];
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                c.eqA[s][a][b] = (real)h->eqA[s][a][b];
+                c.eqX[s][a][b] = (real)h->eqX[s][a][b];
+            }
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                c.eqB[s][a][b] = (real)h->eqB[s][a][b];
+                c.eqH[s][a][b] = (real)h->eqH[s][a][b];
+            }
         for (int r = 0; r < 4; ++r) {
             c.vr[s][r] = (real)sp.v[r];
             c.qr[s][r] = (real)ring_q(sp, r);
+            c.cdx[s][r] = (real)(sp.v[r] * p.dt / p.dx);
+            c.cdy[s][r] = (real)(sp.v[r] * p.dt / p.dy);
         }
-        c.m[s] = (real)sp.m;
-        c.inv_tau[s] = (real)(1.0 / sp.tau);
+        c.mt[s] = (real)(sp.m / sp.tau);
+        c.dpi_tau[s] = (real)((2.0 + sp.I) / sp.tau);
         c.dpi[s] = (real)(2.0 + sp.I);
+        c.inv_m[s] = (real)(1.0 / sp.m);
         c.tau[s] = (real)sp.tau;
-        c.a[s] = (real)sp.a_stoich;
-        c.m_d[s] = sp.m;
-        c.inv_tau_d[s] = 1.0 / sp.tau;
-        c.dpi_d[s] = 2.0 + sp.I;
+        c.dt_tau[s] = (real)(p.dt / sp.tau);
         c.tau_d[s] = sp.tau;
-        c.a_d[s] = sp.a_stoich;
+        c.tau_a[s] = sp.tau * sp.a_stoich;
+        src += (2.0 + sp.I) * sp.a_stoich;
     }
-    c.dt = (real)p.dt;
-    c.dt_dx = (real)(p.dt / p.dx);
-    c.dt_dy = (real)(p.dt / p.dy);
     c.accel_x = (real)p.accel[0];
     c.accel_y = (real)p.accel[1];
     c.k_ov = p.k_ov;
     c.Ea_over_R = p.Ea_over_R;
     c.Qheat = p.Q;
+    c.src = src;
     c.fuel = p.fuel;
     c.oxid = p.oxidizer;
     c.has_reaction = p.k_ov != 0.0;

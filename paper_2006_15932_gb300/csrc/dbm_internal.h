@@ -31,16 +31,20 @@ __host__ __device__ constexpr int dir_y(int i)
 
 // Kernel parameters of the fused step, one block per launch (passed by
 // value as a __grid_constant__; up to 32 KB of parameters are allowed).
+// eqA..eqX are the symmetry blocks of M^-1 (see dbm_step_impl.cuh).
 template <typename real, int S>
 struct StepConsts {
-    real cinv[S][Q][Q];  // M^-1 of each species, row i = velocity, column k = moment
+    real eqA[S][4][4];   // ring means      <- (f1, f4, f5+f7, f14+f16)
+    real eqB[S][2][2];   // axis B (a, c)   <- (f5-f7, f14-f16)
+    real eqH[S][2][2];   // diag H (b, d)   <- (f6, f15)
+    real eqX[S][4][4];   // vector parts    <- (f2, f8, f10, f12) / (f3, f9, f13, f11)
     real vr[S][4];       // ring speeds v_a..v_d
     real qr[S][4];       // v.v + eta^2 of each ring
-    real m[S], inv_tau[S], dpi[S], tau[S], a[S];
-    real dt, dt_dx, dt_dy;
+    real cdx[S][4], cdy[S][4];  // v_r dt/dx, v_r dt/dy
+    real mt[S], dpi_tau[S], dpi[S], inv_m[S], tau[S], dt_tau[S];
     real accel_x, accel_y;
-    double m_d[S], inv_tau_d[S], dpi_d[S], tau_d[S], a_d[S];
-    double k_ov, Ea_over_R, Qheat;
+    double tau_d[S], tau_a[S];  // tau^s, tau^s a^s
+    double k_ov, Ea_over_R, Qheat, src;  // src = sum_s (D+I^s) a^s
     int fuel, oxid;
     int has_reaction, has_force;
     int nx, ny, pitch, bc_x, bc_y;
@@ -64,6 +68,10 @@ struct OutConsts {
 struct dbm_handle {
     dbm_params p;
     double cinv[DBM_MAX_SPECIES][16][16];  // host FP64 M^-1 per species
+    double eqA[DBM_MAX_SPECIES][4][4];     // symmetry blocks of M^-1
+    double eqB[DBM_MAX_SPECIES][2][2];
+    double eqH[DBM_MAX_SPECIES][2][2];
+    double eqX[DBM_MAX_SPECIES][4][4];
     dbm_layout lay;
     void *f[2];
     int cur;

@@ -1,159 +1,401 @@
 // dbm_step_impl.cuh -- the fused per-timestep update of the D2V16 DBM.
 //
-// One thread owns one cell and, in one pass, computes (section "Discrete
-// Boltzmann model" and section "Numerical simulation" of arXiv 2006.15932):
-//   1. species moments n^s, n^s u^s, E^s = sum f (v.v + eta^2);
-//   2. mixture u, T for which the collision conserves momentum and energy;
+// One thread owns two horizontally adjacent cells (x0, y), (x0+1, y) and,
+// in one pass over HBM, computes (section "Discrete Boltzmann model" and
+// section "Numerical simulation" of arXiv 2006.15932):
+//   1. species moments n^s, n^s u^s, E^s = sum f (v.v + eta^2) by ring sums;
+//   2. mixture u, T for which the collision conserves momentum and energy
+//      (the energy-minus-kinetic subtraction of T in FP64);
 //   3. the one-step Arrhenius rate and the post-reaction n^s*, T*;
 //   4. the merged equilibrium f^eq,tot = M^-1 [f-hat(n*, u, T*)
 //      + f-hat(n, u^dag, T^s) - f-hat(n, u^s, T^s)], so that
 //      Omega + R + G = (f^eq,tot - f) / tau (Eqs. CollisionTerm,
-//      ReactionTerm, ForceTerm: f^eq is linear in f-hat);
-//   5. the NND flux differences of v_i . grad f along x and y;
-//   6. the forward-Euler update, stored to the other buffer together with
+//      ReactionTerm, ForceTerm: f^eq is linear in f-hat).  M^-1 is applied
+//      in the symmetry-adapted basis of D2V16 (see below): 56 multiply-adds
+//      instead of 256;
+//   5. the NND flux differences of v_i . grad f along x (faces shared by
+//      the two cells) and y;
+//   6. the forward-Euler update, stored as a pair to the other buffer with
 //      the ghost images the boundary conditions ask for.
+//
+// Symmetry-adapted equilibrium.  Each ring of four velocities splits into
+// a ring mean A, a vector part (E_x, E_y on the axis rings, G_x, G_y on the
+// diagonal rings) and a quadrupole part (B ~ x^2 - y^2 on the axis rings,
+// H ~ xy on the diagonal rings):
+//   axis ring:     f(+x) = A + Ex + B, f(+y) = A + Ey - B,
+//                  f(-x) = A - Ex + B, f(-y) = A - Ey - B;
+//   diagonal ring: f(s_x v, s_y v) = A + s_x Gx + s_y Gy + s_x s_y H.
+// The 16 moment relations f-hat = M f then decouple into independent
+// systems: the ring means from (f1, f4, f5+f7, f14+f16), the two B from
+// (f5-f7, f14-f16), the two H from (f6, f15), the x vector parts from
+// (f2, f8, f10, f12) and the y vector parts from (f3, f9, f13, f11) with
+// the same 4x4 matrix (f-hat indices 1-based as printed).  The host inverts
+// these blocks in FP64 to correct rounding and checks that they reproduce
+// the full M^-1.
 #pragma once
 #include "dbm_consts.h"
 #include "dbm_device.cuh"
 
 namespace dbm {
 
+template <typename real>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using t = float2;
+};
+template <>
+struct Vec2<double> {
+    using t = double2;
+};
+
+template <typename real>
+__device__ __forceinline__ typename Vec2<real>::t ld2(const real *p)
+{
+    return __ldg(reinterpret_cast<const typename Vec2<real>::t *>(p));
+}
+
+// The 16 combinations of f-hat that feed the symmetry blocks, for one cell:
+// c[0..3] ring-mean system, c[4..5] B system, c[6..7] H system,
+// c[8..11] x-vector system, c[12..15] y-vector system.
+template <typename real>
+__device__ __forceinline__ void fhat_blocks(real n, real ux, real uy, real th, real dpi, real c[16])
+{
+    const real xx = ux * ux, yy = uy * uy, u2 = xx + yy;
+    const real a2 = (dpi + real(2)) * th + u2;  // (D+I+2) T/m + u.u
+    const real a4 = (dpi + real(4)) * th + u2;  // (D+I+4) T/m + u.u
+    const real nux = n * ux, nuy = n * uy, nxy = nux * uy, nd = n * (xx - yy);
+    c[0] = n;                                    // f1
+    c[1] = n * (dpi * th + u2);                  // f4
+    c[2] = n * (real(2) * th + u2);              // f5 + f7
+    c[3] = n * (real(2) * a2 * th + u2 * a4);    // f14 + f16
+    c[4] = nd;                                   // f5 - f7
+    c[5] = nd * a4;                              // f14 - f16
+    c[6] = nxy;                                  // f6
+    c[7] = nxy * a4;                             // f15
+    c[8] = nux;                                  // f2
+    c[9] = nux * a2;                             // f8
+    c[10] = nux * (real(3) * th + xx);           // f10
+    c[11] = nux * (th + yy);                     // f12
+    c[12] = nuy;                                 // f3
+    c[13] = nuy * a2;                            // f9
+    c[14] = nuy * (real(3) * th + yy);           // f13
+    c[15] = nuy * (th + xx);                     // f11
+}
+
+// Solve the symmetry blocks: out = ring means A[4], B[2], H[2], X[4], Y[4].
 template <typename real, int S>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void solve_blocks(const StepConsts<real, S> &k, int s, const real c[16],
+                                             real o[16])
+{
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        o[r] = k.eqA[s][r][0] * c[0] + k.eqA[s][r][1] * c[1] + k.eqA[s][r][2] * c[2] +
+               k.eqA[s][r][3] * c[3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        o[4 + r] = k.eqB[s][r][0] * c[4] + k.eqB[s][r][1] * c[5];
+        o[6 + r] = k.eqH[s][r][0] * c[6] + k.eqH[s][r][1] * c[7];
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        o[8 + r] = k.eqX[s][r][0] * c[8] + k.eqX[s][r][1] * c[9] + k.eqX[s][r][2] * c[10] +
+                   k.eqX[s][r][3] * c[11];
+        o[12 + r] = k.eqX[s][r][0] * c[12] + k.eqX[s][r][1] * c[13] + k.eqX[s][r][2] * c[14] +
+                    k.eqX[s][r][3] * c[15];
+    }
+}
+
+// f^eq of velocity i from the block solution o (see the header comment).
+template <typename real>
+__device__ __forceinline__ real feq_of(int i, const real o[16])
+{
+    const int r = i >> 2, k = i & 3;
+    const real A = o[r], X = o[8 + r], Y = o[12 + r];
+    if ((r & 1) == 0) {  // axis ring: B = o[4 + r/2]
+        const real B = o[4 + (r >> 1)];
+        return k == 0 ? A + X + B : k == 1 ? A + Y - B : k == 2 ? A - X + B : A - Y - B;
+    }
+    const real H = o[6 + (r >> 1)];  // diagonal ring
+    return k == 0 ? A + X + Y + H : k == 1 ? A - X + Y - H : k == 2 ? A - X - Y + H : A + X - Y - H;
+}
+
+// NND face values (flux / c) for the two cells x0, x0+1 along x, from
+// f[x0-2 .. x0+3] (pairs L, C, R); returns (H_{j+1/2} - H_{j-1/2}) / c for
+// both cells.  Faces shared by the two cells are computed once.
+template <typename real>
+__device__ __forceinline__ void nnd_x_pair(int sgn, real l0, real l1, real c0, real c1, real r0, real r1,
+                                           real &o0, real &o1)
+{
+    // f_{x0-2}=l0, f_{x0-1}=l1, f_{x0}=c0, f_{x0+1}=c1, f_{x0+2}=r0, f_{x0+3}=r1
+    if (sgn > 0) {
+        const real dm32 = l1 - l0, dm12 = c0 - l1, dp12 = c1 - c0, dp32 = r0 - c1;
+        const real hm = l1 + real(0.5) * minmod(dm32, dm12);  // face x0 - 1/2
+        const real h0 = c0 + real(0.5) * minmod(dm12, dp12);  // face x0 + 1/2
+        const real hp = c1 + real(0.5) * minmod(dp12, dp32);  // face x0 + 3/2
+        o0 = h0 - hm;
+        o1 = hp - h0;
+    } else {
+        const real dm12 = c0 - l1, dp12 = c1 - c0, dp32 = r0 - c1, dp52 = r1 - r0;
+        const real hm = c0 - real(0.5) * minmod(dm12, dp12);  // face x0 - 1/2
+        const real h0 = c1 - real(0.5) * minmod(dp12, dp32);  // face x0 + 1/2
+        const real hp = r0 - real(0.5) * minmod(dp32, dp52);  // face x0 + 3/2
+        o0 = h0 - hm;
+        o1 = hp - h0;
+    }
+}
+
+// Ghost-image bitmask of interior index k on an axis of n cells: bit j set
+// when ghost index {-2, -1, n, n+1}[j] takes its value from cell k.
+__device__ __forceinline__ unsigned ghost_mask(int k, int n, int bc)
+{
+    unsigned m = 0;
+    if (bc == DBM_BC_PERIODIC) {
+        if ((((-2 % n) + n) % n) == k) m |= 1u;
+        if ((((-1 % n) + n) % n) == k) m |= 2u;
+        if ((n % n) == k) m |= 4u;
+        if (((n + 1) % n) == k) m |= 8u;
+    } else {
+        if (k == 0) m |= 3u;
+        if (k == n - 1) m |= 12u;
+    }
+    return m;
+}
+
+__device__ __forceinline__ int ghost_index(int j, int n) { return j < 2 ? j - 2 : n + (j - 2); }
+
+template <typename real>
+__device__ __forceinline__ void store_images(real *pl, int x, int y, int nx, int ny, int pitch,
+                                             unsigned mx, unsigned my, real v)
+{
+    for (int j = 0; j < 4; ++j) {
+        if (mx & (1u << j)) pl[(long long)(y + GY) * pitch + (ghost_index(j, nx) + GX)] = v;
+        if (my & (1u << j)) pl[(long long)(ghost_index(j, ny) + GY) * pitch + (x + GX)] = v;
+    }
+}
+
+template <typename real, int S>
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 2 : 1)
     k_step(const __grid_constant__ StepConsts<real, S> c, const real *__restrict__ fin,
            real *__restrict__ fout, unsigned *__restrict__ flag)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    using R2 = typename Vec2<real>::t;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= c.nx || y >= c.ny) return;
+    if (x0 >= c.nx || y >= c.ny) return;
+    const bool two = x0 + 1 < c.nx;
     const long long P = c.plane;
-    const long long cell = (long long)(y + GY) * c.pitch + (x + GX);
+    const long long cell = (long long)(y + GY) * c.pitch + (x0 + GX);
+    const long long py = c.pitch;
 
-    // 1. species moments, by ring sums
-    real n[S], jx[S], jy[S], en[S];
+    // 1. species moments of both cells, by ring sums
+    real n0[S], n1[S], cap0 = 0, cap1 = 0;
+    real w0 = 0, w1 = 0, wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0, we0 = 0, we1 = 0, wd0 = 0, wd1 = 0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        real sn = 0, sx = 0, sy = 0, se = 0;
+        real sn0 = 0, sn1 = 0, sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0, se0 = 0, se1 = 0;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            real rs = 0, rx = 0, ry = 0;
+            real rs0 = 0, rs1 = 0, rx0 = 0, rx1 = 0, ry0 = 0, ry1 = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int i = 4 * r + k;
-                const real f = fin[(s * Q + i) * P + cell];
-                rs += f;
-                rx += dir_x(i) * f;
-                ry += dir_y(i) * f;
+                const R2 f = ld2(fin + (s * Q + i) * P + cell);
+                rs0 += f.x;
+                rs1 += f.y;
+                if (dir_x(i) > 0) { rx0 += f.x; rx1 += f.y; }
+                if (dir_x(i) < 0) { rx0 -= f.x; rx1 -= f.y; }
+                if (dir_y(i) > 0) { ry0 += f.x; ry1 += f.y; }
+                if (dir_y(i) < 0) { ry0 -= f.x; ry1 -= f.y; }
             }
-            sn += rs;
-            sx += c.vr[s][r] * rx;
-            sy += c.vr[s][r] * ry;
-            se += c.qr[s][r] * rs;
+            sn0 += rs0;
+            sn1 += rs1;
+            sx0 += c.vr[s][r] * rx0;
+            sx1 += c.vr[s][r] * rx1;
+            sy0 += c.vr[s][r] * ry0;
+            sy1 += c.vr[s][r] * ry1;
+            se0 += c.qr[s][r] * rs0;
+            se1 += c.qr[s][r] * rs1;
         }
-        n[s] = sn;
-        jx[s] = sx;
-        jy[s] = sy;
-        en[s] = se;
+        n0[s] = sn0;
+        n1[s] = sn1;
+        const real mt = c.mt[s];  // m / tau
+        w0 += mt * sn0;
+        w1 += mt * sn1;
+        wx0 += mt * sx0;
+        wx1 += mt * sx1;
+        wy0 += mt * sy0;
+        wy1 += mt * sy1;
+        we0 += mt * se0;
+        we1 += mt * se1;
+        wd0 += c.dpi_tau[s] * sn0;
+        wd1 += c.dpi_tau[s] * sn1;
+        cap0 += c.dpi[s] * sn0;
+        cap1 += c.dpi[s] * sn1;
     }
 
-    // 2. mixture velocity and temperature (temperature always in FP64)
-    real w = 0, wx = 0, wy = 0;
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const real mt = c.m[s] * c.inv_tau[s];
-        w += mt * n[s];
-        wx += mt * jx[s];
-        wy += mt * jy[s];
+    // 2. mixture velocity; temperature T = (W - u.u w) / (sum n (D+I)/tau)
+    //    with the cancelling subtraction in FP64
+    const real ux0 = wx0 / w0, uy0 = wy0 / w0, ux1 = wx1 / w1, uy1 = wy1 / w1;
+    double T0, T1;
+    {
+        const double u20 = (double)ux0 * (double)ux0 + (double)uy0 * (double)uy0;
+        const double u21 = (double)ux1 * (double)ux1 + (double)uy1 * (double)uy1;
+        const double num0 = (double)we0 - u20 * (double)w0;
+        const double num1 = (double)we1 - u21 * (double)w1;
+        if (sizeof(real) == 8) {
+            T0 = num0 / (double)wd0;
+            T1 = num1 / (double)wd1;
+        } else {
+            T0 = num0 * (double)(real(1) / wd0);
+            T1 = num1 * (double)(real(1) / wd1);
+        }
     }
-    const real ux = wx / w, uy = wy / w;
-    const double u2 = (double)ux * (double)ux + (double)uy * (double)uy;
-    double num = 0.0, den = 0.0;
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-        num += (c.m_d[s] * (double)en[s] - c.m_d[s] * (double)n[s] * u2) * c.inv_tau_d[s];
-        den += (double)n[s] * c.dpi_d[s] * c.inv_tau_d[s];
-    }
-    const double Td = num / den;
 
-    // health: a species may be absent (n = 0) or slightly negative from
-    // numerical diffusion; flag densities below -1e-6 of the mixture
     unsigned bad = 0;
-    real nabs = 0;
-#pragma unroll
-    for (int s = 0; s < S; ++s) nabs += fabs(n[s]);
-#pragma unroll
-    for (int s = 0; s < S; ++s)
-        if (!(n[s] >= real(-1e-6) * nabs)) bad |= DBM_HEALTH_DENSITY;
-    if (!(nabs > real(0))) bad |= DBM_HEALTH_DENSITY;
-    if (!(Td > 0.0)) bad |= DBM_HEALTH_TEMPERATURE;
-    if (!isfinite(Td) || !isfinite((double)ux) || !isfinite((double)uy)) bad |= DBM_HEALTH_NONFINITE;
-
-    // 3. reaction: omega_ov and T' (reading: state after a time tau^s)
-    double omega = 0.0, dTdt = 0.0;
-    if (c.has_reaction) {
-        const double nf = (double)n[c.fuel], no = (double)n[c.oxid];
-        omega = c.k_ov * nf * no * exp(-c.Ea_over_R / Td);
-        double src = 0.0, cap = 0.0;
+    real a0 = 0, a1 = 0;  // sum_s |n^s| of both cells
+    {
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            src += c.dpi_d[s] * c.a_d[s];
-            cap += (double)n[s] * c.dpi_d[s];
+            a0 += fabs(n0[s]);
+            a1 += fabs(n1[s]);
         }
-        dTdt = (c.Qheat - 0.5 * Td * src) * omega / (0.5 * cap);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            if (!(n0[s] >= real(-1e-6) * a0) || !(n1[s] >= real(-1e-6) * a1)) bad |= DBM_HEALTH_DENSITY;
+        if (!(a0 > real(0)) || !(a1 > real(0))) bad |= DBM_HEALTH_DENSITY;
+        if (!(T0 > 0.0) || !(T1 > 0.0)) bad |= DBM_HEALTH_TEMPERATURE;
+        if (!isfinite(T0) || !isfinite(T1) || !isfinite((double)(ux0 + uy0 + ux1 + uy1)))
+            bad |= DBM_HEALTH_NONFINITE;
     }
 
-    const Images im = cell_images(x, y, c.nx, c.ny, c.bc_x, c.bc_y);
+    // 3. reaction: omega_ov and T' (state after a time tau^s), FP64
+    double om0 = 0.0, om1 = 0.0, dT0 = 0.0, dT1 = 0.0;
+    if (c.has_reaction) {
+        om0 = c.k_ov * (double)n0[c.fuel] * (double)n0[c.oxid] * exp(-c.Ea_over_R / T0);
+        om1 = c.k_ov * (double)n1[c.fuel] * (double)n1[c.oxid] * exp(-c.Ea_over_R / T1);
+        dT0 = (c.Qheat - 0.5 * T0 * c.src) * om0 / (0.5 * (double)cap0);
+        dT1 = (c.Qheat - 0.5 * T1 * c.src) * om1 / (0.5 * (double)cap1);
+    }
 
-#pragma unroll
+    const unsigned mx0 = ghost_mask(x0, c.nx, c.bc_x), mx1 = two ? ghost_mask(x0 + 1, c.nx, c.bc_x) : 0u;
+    const unsigned my = ghost_mask(y, c.ny, c.bc_y);
+    const bool images = (mx0 | mx1 | my) != 0u;
+
+#pragma unroll 1
     for (int s = 0; s < S; ++s) {
-        // 4. merged equilibrium moments
-        real fh[Q];
-        real ns = n[s];
-        double Ts = Td;
-        if (c.has_reaction) {
-            const double nstar = (double)n[s] + c.tau_d[s] * c.a_d[s] * omega;
-            if (nstar < 0.0) bad |= DBM_HEALTH_NSTAR;
-            ns = (real)nstar;
-            Ts = Td + c.tau_d[s] * dTdt;
-        }
-        const real inv_m = real(1) / c.m[s];
-        fhat16<real>(ns, ux, uy, (real)Ts * inv_m, c.dpi[s], fh);
-        if (c.has_force && n[s] != real(0)) {  // an absent species feels no force
-            const real usx = jx[s] / n[s], usy = jy[s] / n[s];
-            const real ths = (en[s] / n[s] - (usx * usx + usy * usy)) / c.dpi[s];
-            real g1[Q], g0[Q];
-            fhat16<real>(n[s], usx + c.accel_x * c.tau[s], usy + c.accel_y * c.tau[s], ths, c.dpi[s], g1);
-            fhat16<real>(n[s], usx, usy, ths, c.dpi[s], g0);
+        const real *fs = fin + (long long)(s * Q) * P + cell;
+        real *gs = fout + (long long)(s * Q) * P + cell;
+        // centres of this species, both cells
+        real f0[Q], f1[Q];
 #pragma unroll
-            for (int k = 0; k < Q; ++k) fh[k] += g1[k] - g0[k];
+        for (int i = 0; i < Q; ++i) {
+            const R2 v = ld2(fs + i * P);
+            f0[i] = v.x;
+            f1[i] = v.y;
         }
-        const real dt_tau = c.dt * c.inv_tau[s];
+        // 4. merged equilibrium moments of both cells
+        real cb0[16], cb1[16];
+        {
+            real ns0 = 0, ns1 = 0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                ns0 += f0[i];
+                ns1 += f1[i];
+            }
+            real nr0 = ns0, nr1 = ns1;
+            double Ts0 = T0, Ts1 = T1;
+            if (c.has_reaction) {
+                const double e0 = (double)ns0 + c.tau_a[s] * om0, e1 = (double)ns1 + c.tau_a[s] * om1;
+                if (e0 < -1e-6 * (double)a0 || e1 < -1e-6 * (double)a1) bad |= DBM_HEALTH_NSTAR;
+                nr0 = (real)e0;
+                nr1 = (real)e1;
+                Ts0 = T0 + c.tau_d[s] * dT0;
+                Ts1 = T1 + c.tau_d[s] * dT1;
+            }
+            fhat_blocks<real>(nr0, ux0, uy0, (real)Ts0 * c.inv_m[s], c.dpi[s], cb0);
+            fhat_blocks<real>(nr1, ux1, uy1, (real)Ts1 * c.inv_m[s], c.dpi[s], cb1);
+            if (c.has_force) {
+                // species velocity and temperature from this species' moments
+                real jx0 = 0, jx1 = 0, jy0 = 0, jy1 = 0, e0 = 0, e1 = 0;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const real vx = dir_x(i) * c.vr[s][i >> 2], vy = dir_y(i) * c.vr[s][i >> 2];
+                    jx0 += vx * f0[i];
+                    jx1 += vx * f1[i];
+                    jy0 += vy * f0[i];
+                    jy1 += vy * f1[i];
+                    e0 += c.qr[s][i >> 2] * f0[i];
+                    e1 += c.qr[s][i >> 2] * f1[i];
+                }
+                real g[16], h[16];
+                if (ns0 != real(0)) {
+                    const real usx = jx0 / ns0, usy = jy0 / ns0;
+                    const real th = (e0 / ns0 - (usx * usx + usy * usy)) / c.dpi[s];
+                    fhat_blocks<real>(ns0, usx + c.accel_x * c.tau[s], usy + c.accel_y * c.tau[s], th,
+                                      c.dpi[s], g);
+                    fhat_blocks<real>(ns0, usx, usy, th, c.dpi[s], h);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) cb0[k] += g[k] - h[k];
+                }
+                if (ns1 != real(0)) {
+                    const real usx = jx1 / ns1, usy = jy1 / ns1;
+                    const real th = (e1 / ns1 - (usx * usx + usy * usy)) / c.dpi[s];
+                    fhat_blocks<real>(ns1, usx + c.accel_x * c.tau[s], usy + c.accel_y * c.tau[s], th,
+                                      c.dpi[s], g);
+                    fhat_blocks<real>(ns1, usx, usy, th, c.dpi[s], h);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) cb1[k] += g[k] - h[k];
+                }
+            }
+        }
+        real o0[16], o1[16];
+        solve_blocks<real, S>(c, s, cb0, o0);
+        solve_blocks<real, S>(c, s, cb1, o1);
+        const real dtt = c.dt_tau[s];
 
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            real feq = 0;
-#pragma unroll
-            for (int k = 0; k < Q; ++k) feq += c.cinv[s][i][k] * fh[k];
-
-            const real *pl = fin + (s * Q + i) * P;
-            const real f0 = pl[cell];
+            const real *pl = fs + i * P;
             const int r = i >> 2;
-            // 5. NND advection, -dt (v_x d/dx + v_y d/dy) f
-            real adv = 0;
-            if (dir_x(i) > 0)
-                adv += c.vr[s][r] * c.dt_dx * nnd_diff_pos(pl[cell - 2], pl[cell - 1], f0, pl[cell + 1]);
-            else if (dir_x(i) < 0)
-                adv -= c.vr[s][r] * c.dt_dx * nnd_diff_neg(pl[cell - 1], f0, pl[cell + 1], pl[cell + 2]);
-            const long long py = c.pitch;
-            if (dir_y(i) > 0)
-                adv += c.vr[s][r] * c.dt_dy *
-                       nnd_diff_pos(pl[cell - 2 * py], pl[cell - py], f0, pl[cell + py]);
-            else if (dir_y(i) < 0)
-                adv -= c.vr[s][r] * c.dt_dy *
-                       nnd_diff_neg(pl[cell - py], f0, pl[cell + py], pl[cell + 2 * py]);
-            // 6. forward Euler
-            const real f1 = f0 + dt_tau * (feq - f0) - adv;
-            store_with_images(fout + (s * Q + i) * P, cell, x, y, c.pitch, im, f1);
+            real a0 = 0, a1 = 0;  // dt * v . grad f of both cells
+            // 5. NND advection
+            if (dir_x(i) != 0) {
+                const R2 L = ld2(pl - 2), Rr = ld2(pl + 2);
+                real d0, d1;
+                nnd_x_pair<real>(dir_x(i), L.x, L.y, f0[i], f1[i], Rr.x, Rr.y, d0, d1);
+                const real cx = dir_x(i) * c.cdx[s][r];
+                a0 += cx * d0;
+                a1 += cx * d1;
+            }
+            if (dir_y(i) > 0) {
+                const R2 m2 = ld2(pl - 2 * py), m1 = ld2(pl - py), p1 = ld2(pl + py);
+                const real cy = c.cdy[s][r];
+                a0 += cy * nnd_diff_pos(m2.x, m1.x, f0[i], p1.x);
+                a1 += cy * nnd_diff_pos(m2.y, m1.y, f1[i], p1.y);
+            } else if (dir_y(i) < 0) {
+                const R2 m1 = ld2(pl - py), p1 = ld2(pl + py), p2 = ld2(pl + 2 * py);
+                const real cy = c.cdy[s][r];
+                a0 -= cy * nnd_diff_neg(m1.x, f0[i], p1.x, p2.x);
+                a1 -= cy * nnd_diff_neg(m1.y, f1[i], p1.y, p2.y);
+            }
+            // 6. forward Euler: f + dt/tau (f^eq,tot - f) - dt v . grad f
+            const real g0 = f0[i] + dtt * (feq_of<real>(i, o0) - f0[i]) - a0;
+            const real g1 = f1[i] + dtt * (feq_of<real>(i, o1) - f1[i]) - a1;
+            real *po = gs + i * P;
+            if (two) {
+                R2 v;
+                v.x = g0;
+                v.y = g1;
+                *reinterpret_cast<R2 *>(po) = v;
+            } else {
+                *po = g0;
+            }
+            if (images) {
+                real *plo = fout + (long long)(s * Q + i) * P;
+                store_images(plo, x0, y, c.nx, c.ny, c.pitch, mx0, my, g0);
+                if (two) store_images(plo, x0 + 1, y, c.nx, c.ny, c.pitch, mx1, my, g1);
+            }
         }
     }
     if (bad) raise_flag(flag, bad);
@@ -165,9 +407,8 @@ int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st)
     StepConsts<real, S> c;
     fill_step_consts<real, S>(h, c);
     dim3 block(32, 8);
-    dim3 grid((h->p.nx + 31) / 32, (h->p.ny + 7) / 8);
-    k_step<real, S><<<grid, block, 0, st>>>(c, (const real *)fin, (real *)fout,
-                                            (unsigned *)h->scratch);
+    dim3 grid((h->p.nx + 63) / 64, (h->p.ny + 7) / 8);
+    k_step<real, S><<<grid, block, 0, st>>>(c, (const real *)fin, (real *)fout, (unsigned *)h->scratch);
     return set_cuda_error(h, cudaGetLastError(), "step kernel launch");
 }
 
