@@ -61,7 +61,8 @@ enum dbm_status_code {
     DBM_ERR_CUDA = -4,        /* a CUDA runtime call or launch failed           */
     DBM_ERR_NONFINITE = -5,   /* device health flag: a non-finite moment        */
     DBM_ERR_NEGATIVE = -6,    /* device health flag: negative density, T <= 0 or n* < 0 */
-    DBM_ERR_STABILITY = -7    /* CFL or dt/tau stability limit exceeded         */
+    DBM_ERR_STABILITY = -7,   /* CFL or dt/tau stability limit exceeded         */
+    DBM_ERR_TIMEOUT = -8      /* device health flag: a bounded wait gave up     */
 };
 
 /* Health-flag bits as kept on the device (dbm_status_bits). */
@@ -69,7 +70,15 @@ enum dbm_health_bits {
     DBM_HEALTH_DENSITY = 1,      /* n^s < -1e-6 sum|n^s|, no matter at all, or not finite */
     DBM_HEALTH_TEMPERATURE = 2,  /* mixture T <= 0 or not finite */
     DBM_HEALTH_NSTAR = 4,        /* n^s* < 0 after the reaction  */
-    DBM_HEALTH_NONFINITE = 8     /* a non-finite moment           */
+    DBM_HEALTH_NONFINITE = 8,    /* a non-finite moment           */
+    DBM_HEALTH_TIMEOUT = 16      /* a tile copy did not complete within its wait limit */
+};
+
+/* Step kernel selection (dbm_params.step_kernel). */
+enum dbm_step_kernel {
+    DBM_KERNEL_AUTO = 0,     /* TMA-staged where built (FP32, S <= 3), else generic */
+    DBM_KERNEL_GENERIC = 1,  /* stencil read from global memory                      */
+    DBM_KERNEL_TMA = 2       /* tile + halo staged in shared memory by one TMA copy  */
 };
 
 /* Constants of one species sigma. */
@@ -95,6 +104,7 @@ typedef struct dbm_params {
     double Q;               /* heat released per mole of reaction                   */
     double accel[2];        /* external acceleration a of the force term; 0 = off   */
     int precision;          /* dbm_precision                                         */
+    int step_kernel;        /* dbm_step_kernel; both give bitwise identical results  */
     dbm_species sp[DBM_MAX_SPECIES];
 } dbm_params;
 

@@ -260,6 +260,8 @@ static int validate(dbm_handle *h, const dbm_params &p)
     }
     if (p.precision != DBM_FP64 && p.precision != DBM_FP32 && p.precision != DBM_BF16DEV)
         return fail(h, DBM_ERR_INVALID, "unknown precision %d", p.precision);
+    if (p.step_kernel < DBM_KERNEL_AUTO || p.step_kernel > DBM_KERNEL_TMA)
+        return fail(h, DBM_ERR_INVALID, "unknown step kernel %d", p.step_kernel);
     if (!isfinite(p.accel[0]) || !isfinite(p.accel[1]))
         return fail(h, DBM_ERR_INVALID, "acceleration must be finite");
     double vmax = 0.0;
@@ -451,6 +453,9 @@ int dbm_bind(dbm_handle *h, void *f_a, void *f_b, void *scratch)
     h->scratch = scratch;
     h->cur = 0;
     h->bound = 1;
+    make_tensor_maps(h);
+    if (h->p.step_kernel == DBM_KERNEL_TMA && !h->tma_ok)
+        return fail(h, DBM_ERR_INVALID, "the TMA-staged step kernel is built for FP32 with at most 3 species");
     return DBM_OK;
 }
 
@@ -504,7 +509,7 @@ int dbm_step(dbm_handle *h, int nsteps, void *stream)
     if (nsteps < 0) return fail(h, DBM_ERR_INVALID, "nsteps=%d < 0", nsteps);
     cudaStream_t st = (cudaStream_t)stream;
     for (int t = 0; t < nsteps; ++t) {
-        rc = launch_step(h, h->f[h->cur], h->f[h->cur ^ 1], st);
+        rc = launch_step(h, h->cur, st);
         if (rc) return rc;
         h->cur ^= 1;
         h->steps += 1;
@@ -548,6 +553,7 @@ int dbm_status(dbm_handle *h, void *stream, unsigned *bits)
     rc = set_cuda_error(h, cudaStreamSynchronize(st), "synchronise for health flag");
     if (rc) return rc;
     if (bits) *bits = v;
+    if (v & DBM_HEALTH_TIMEOUT) return fail(h, DBM_ERR_TIMEOUT, "a tile copy timed out (flag %u)", v);
     if (v & DBM_HEALTH_NONFINITE) return fail(h, DBM_ERR_NONFINITE, "non-finite moment (flag %u)", v);
     if (v) return fail(h, DBM_ERR_NEGATIVE, "non-positive density/temperature or negative n* (flag %u)", v);
     return DBM_OK;

@@ -37,6 +37,8 @@ void fill_step_consts(const dbm_handle *h, StepConsts<real, S> &c)
         for (int r = 0; r < 4; ++r) {
             c.vr[s][r] = (real)sp.v[r];
             c.qr[s][r] = (real)ring_q(sp, r);
+            c.q4[s][r] = (real)(4.0 * ring_q(sp, r));
+            c.wv[s][r] = (real)(((r & 1) ? 4.0 : 2.0) * sp.v[r]);
             c.cdx[s][r] = (real)(sp.v[r] * p.dt / p.dx);
             c.cdy[s][r] = (real)(sp.v[r] * p.dt / p.dy);
         }

@@ -45,8 +45,11 @@ __device__ __forceinline__ double minmod(double a, double b)
 }
 __device__ __forceinline__ float minmod(float a, float b)
 {
-    const float s = copysignf(1.0f, a);
-    return s * fmaxf(fminf(fabsf(a), s * b), 0.0f);
+    // t = min(|a|, |b|) carrying the sign (sgn a) xor (sgn b): positive
+    // exactly when a and b agree in sign
+    float t;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(t) : "f"(a), "f"(b));
+    return copysignf(fmaxf(t, 0.0f), a);
 }
 
 // NND flux difference along one axis for a velocity component of sign

@@ -3,6 +3,7 @@
 // launchers.  Not part of the public ABI (include/dbm.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,6 +41,8 @@ struct StepConsts {
     real eqX[S][4][4];   // vector parts    <- (f2, f8, f10, f12) / (f3, f9, f13, f11)
     real vr[S][4];       // ring speeds v_a..v_d
     real qr[S][4];       // v.v + eta^2 of each ring
+    real q4[S][4];       // 4 (v.v + eta^2): energy of a unit ring mean
+    real wv[S][4];       // 2 v_r (axis) or 4 v_r (diagonal): momentum of a unit vector part
     real cdx[S][4], cdy[S][4];  // v_r dt/dx, v_r dt/dy
     real mt[S], dpi_tau[S], dpi[S], inv_m[S], tau[S], dt_tau[S];
     real accel_x, accel_y;
@@ -67,6 +70,8 @@ struct OutConsts {
 
 struct dbm_handle {
     dbm_params p;
+    CUtensorMap tmap[2];  // TMA descriptors of the two bound state buffers
+    int tma_ok;           // the TMA-staged step kernel can run
     double cinv[DBM_MAX_SPECIES][16][16];  // host FP64 M^-1 per species
     double eqA[DBM_MAX_SPECIES][4][4];     // symmetry blocks of M^-1
     double eqB[DBM_MAX_SPECIES][2][2];
@@ -84,7 +89,8 @@ struct dbm_handle {
 namespace dbm {
 
 // Launchers; each returns DBM_OK or DBM_ERR_CUDA (message in h->err).
-int launch_step(dbm_handle *h, const void *fin, void *fout, cudaStream_t st);
+int launch_step(dbm_handle *h, int cur, cudaStream_t st);
+int make_tensor_maps(dbm_handle *h);
 int launch_set_state(dbm_handle *h, void *f, const double *rho_s, const double *ux,
                      const double *uy, const double *T, cudaStream_t st);
 int launch_set_f(dbm_handle *h, void *f, const double *src, cudaStream_t st);

@@ -1,15 +1,69 @@
-// dbm_step.cu -- dispatch of the fused step on precision and species count;
-// the kernel itself is in dbm_step_impl.cuh, instantiated once per species
-// count in dbm_step_s<S>.cu so that the units compile in parallel.
+// dbm_step.cu -- dispatch of the fused step on precision, species count and
+// kernel variant, and the TMA descriptors of the state buffers.  The
+// kernels are in dbm_step_impl.cuh, instantiated once per species count in
+// dbm_step_s<S>.cu so that the units compile in parallel.
+#include <string.h>
+
 #include "dbm_internal.h"
 
 namespace dbm {
 
 template <typename real, int S>
 int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st);
+template <typename real, int S, int TX, int TY>
+int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, void *fout, cudaStream_t st);
+
+// Tile shapes of the TMA-staged kernel (FP32): 64 x 8 cells for one or two
+// species (110.6 KB of shared memory for two), 32 x 8 for three.
+bool tma_supported(const dbm_params &p) { return p.precision == DBM_FP32 && p.nspecies <= 3; }
+
+static int tma_box(const dbm_params &p, unsigned box[3])
+{
+    const int tx = p.nspecies <= 2 ? 64 : 32, ty = 8;
+    box[0] = tx + 8;
+    box[1] = ty + 4;
+    box[2] = 16 * p.nspecies;
+    return 0;
+}
+
+typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                    CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                    CUtensorMapFloatOOBfill);
+
+// One 3-D descriptor per state buffer: (column, row, plane) with the whole
+// padded geometry; out-of-range boxes are zero-filled by the copy engine.
+int make_tensor_maps(dbm_handle *h)
+{
+    h->tma_ok = 0;
+    if (!tma_supported(h->p)) return DBM_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return DBM_OK;  // no TMA descriptors: the generic kernel runs
+    }
+    encode_tiled_fn encode = (encode_tiled_fn)fn;
+    const dbm_layout &L = h->lay;
+    cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)(16 * h->p.nspecies)};
+    cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
+    cuuint32_t box[3], estr[3] = {1, 1, 1};
+    unsigned b[3];
+    tma_box(h->p, b);
+    for (int i = 0; i < 3; ++i) box[i] = b[i];
+    for (int k = 0; k < 2; ++k) {
+        CUresult r = encode(&h->tmap[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->f[k], dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return DBM_OK;
+    }
+    h->tma_ok = 1;
+    return DBM_OK;
+}
 
 template <typename real>
-static int launch_step_p(dbm_handle *h, const void *fin, void *fout, cudaStream_t st)
+static int launch_generic(dbm_handle *h, const void *fin, void *fout, cudaStream_t st)
 {
     switch (h->p.nspecies) {
     case 1: return launch_step_t<real, 1>(h, fin, fout, st);
@@ -24,10 +78,22 @@ static int launch_step_p(dbm_handle *h, const void *fin, void *fout, cudaStream_
     return DBM_ERR_INVALID;
 }
 
-int launch_step(dbm_handle *h, const void *fin, void *fout, cudaStream_t st)
+int launch_step(dbm_handle *h, int cur, cudaStream_t st)
 {
-    if (h->p.precision == DBM_FP64) return launch_step_p<double>(h, fin, fout, st);
-    if (h->p.precision == DBM_FP32) return launch_step_p<float>(h, fin, fout, st);
+    const void *fin = h->f[cur];
+    void *fout = h->f[cur ^ 1];
+    const int want = h->p.step_kernel;
+    if (h->tma_ok && want != DBM_KERNEL_GENERIC) {
+        const CUtensorMap *tm = &h->tmap[cur];
+        switch (h->p.nspecies) {
+        case 1: return launch_step_tma_t<float, 1, 64, 8>(h, tm, fout, st);
+        case 2: return launch_step_tma_t<float, 2, 64, 8>(h, tm, fout, st);
+        case 3: return launch_step_tma_t<float, 3, 32, 8>(h, tm, fout, st);
+        }
+    }
+    if (want == DBM_KERNEL_TMA) return DBM_ERR_INVALID;
+    if (h->p.precision == DBM_FP64) return launch_generic<double>(h, fin, fout, st);
+    if (h->p.precision == DBM_FP32) return launch_generic<float>(h, fin, fout, st);
     return DBM_ERR_INVALID;
 }
 

@@ -32,7 +32,9 @@ ERRORS = {
     -5: "DBM_ERR_NONFINITE",
     -6: "DBM_ERR_NEGATIVE",
     -7: "DBM_ERR_STABILITY",
+    -8: "DBM_ERR_TIMEOUT",
 }
+KERNELS = {"auto": 0, "generic": 1, "tma": 2}
 EXPORTS = [
     "dbm_init", "dbm_init_error", "dbm_equilibrium_matrix", "dbm_get_layout", "dbm_state_bytes", "dbm_scratch_bytes",
     "dbm_bind", "dbm_set_state", "dbm_set_f", "dbm_get_f", "dbm_step", "dbm_moments",
@@ -75,6 +77,7 @@ class dbm_params(C.Structure):
         ("Q", C.c_double),
         ("accel", C.c_double * 2),
         ("precision", C.c_int),
+        ("step_kernel", C.c_int),
         ("sp", dbm_species * MAX_SPECIES),
     ]
 
@@ -133,7 +136,8 @@ def load(path: str = LIB_PATH):
 
 
 def make_params(nx, ny, species, *, dx, dy, dt, bc_x=PERIODIC, bc_y=PERIODIC, fuel=0, oxid=1,
-                k_ov=0.0, Ea_over_R=0.0, Q=0.0, accel=(0.0, 0.0), precision=FP64) -> dbm_params:
+                k_ov=0.0, Ea_over_R=0.0, Q=0.0, accel=(0.0, 0.0), precision=FP64,
+                step_kernel="auto") -> dbm_params:
     """Fill a dbm_params record; ``species`` items need m, I, tau, v, eta, a."""
     if len(species) > MAX_SPECIES:
         raise ValueError(f"at most {MAX_SPECIES} species")
@@ -145,6 +149,7 @@ def make_params(nx, ny, species, *, dx, dy, dt, bc_x=PERIODIC, bc_y=PERIODIC, fu
     p.k_ov, p.Ea_over_R, p.Q = float(k_ov), float(Ea_over_R), float(Q)
     p.accel[0], p.accel[1] = float(accel[0]), float(accel[1])
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.step_kernel = KERNELS[step_kernel] if isinstance(step_kernel, str) else int(step_kernel)
     for s, sp in enumerate(species):
         c = p.sp[s]
         c.m, c.I, c.tau, c.a_stoich = float(sp.m), float(sp.I), float(sp.tau), float(sp.a)
@@ -154,10 +159,11 @@ def make_params(nx, ny, species, *, dx, dy, dt, bc_x=PERIODIC, bc_y=PERIODIC, fu
     return p
 
 
-def params_from_problem(pb, precision=FP64) -> dbm_params:
+def params_from_problem(pb, precision=FP64, step_kernel="auto") -> dbm_params:
     return make_params(pb.nx, pb.ny, pb.species, dx=pb.dx, dy=pb.dy, dt=pb.dt, bc_x=pb.bc_x,
                        bc_y=pb.bc_y, fuel=pb.fuel, oxid=pb.oxid, k_ov=pb.k_ov,
-                       Ea_over_R=pb.Ea_over_R, Q=pb.Q, accel=pb.accel, precision=precision)
+                       Ea_over_R=pb.Ea_over_R, Q=pb.Q, accel=pb.accel, precision=precision,
+                       step_kernel=step_kernel)
 
 
 # ---------------------------------------------------------------------------
@@ -261,13 +267,13 @@ class Solver:
     """One DBM problem on one GPU: the handle, two state buffers and the
     scratch buffer (torch allocations), and FP64 field transfers."""
 
-    def __init__(self, problem, precision="fp64", device="cuda", stream=None):
+    def __init__(self, problem, precision="fp64", device="cuda", stream=None, step_kernel="auto"):
         import torch
 
         self.torch = torch
         self.pb = problem
         self.device = torch.device(device)
-        self.params = params_from_problem(problem, precision)
+        self.params = params_from_problem(problem, precision, step_kernel)
         self.h = dbm_init(self.params)
         self.layout = dbm_get_layout(self.h)
         nb = dbm_state_bytes(self.h)
