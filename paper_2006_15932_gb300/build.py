@@ -27,6 +27,11 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
               "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
 
 
+# the FP64 reference-order step rounds every operation separately, like the
+# plain FP64 evaluation it is held to
+PER_FILE_FLAGS = {"dbm_step_f64.cu": ["--fmad=false"]}
+
+
 def nvcc() -> str:
     for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -56,7 +61,8 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *PER_FILE_FLAGS.get(os.path.basename(src), []), *extra, "-c", src,
+               "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -42,12 +42,18 @@ void fill_step_consts(const dbm_handle *h, StepConsts<real, S> &c)
             c.cdx[s][r] = (real)(sp.v[r] * p.dt / p.dx);
             c.cdy[s][r] = (real)(sp.v[r] * p.dt / p.dy);
         }
-        c.mt[s] = (real)(sp.m / sp.tau);
-        c.dpi_tau[s] = (real)((2.0 + sp.I) / sp.tau);
         c.dpi[s] = (real)(2.0 + sp.I);
         c.inv_m[s] = (real)(1.0 / sp.m);
         c.tau[s] = (real)sp.tau;
         c.dt_tau[s] = (real)(p.dt / sp.tau);
+        // exact products of the constants as stored (errors ~1e-16), split so
+        // that no rounding of a constant biases the mixture u and T
+        const double lam = sp.m * (double)c.dt_tau[s];
+        const double kap = lam * (double)c.dpi[s] * (double)c.inv_m[s];
+        c.lam_h[s] = (real)lam;
+        c.lam_l[s] = (real)(lam - (double)c.lam_h[s]);
+        c.kap_h[s] = (real)kap;
+        c.kap_l[s] = (real)(kap - (double)c.kap_h[s]);
         c.tau_d[s] = sp.tau;
         c.tau_a[s] = sp.tau * sp.a_stoich;
         src += (2.0 + sp.I) * sp.a_stoich;
@@ -93,6 +99,49 @@ void fill_out_consts(const dbm_handle *h, OutConsts<S> &c)
     c.fuel = p.fuel;
     c.Qheat = p.Q;
     c.abs_a_fuel = c.has_reaction ? fabs(p.sp[p.fuel].a_stoich) : 1.0;
+    c.nx = p.nx;
+    c.ny = p.ny;
+    c.pitch = h->lay.pitch;
+    c.bc_x = p.bc_x;
+    c.bc_y = p.bc_y;
+    c.plane = h->lay.plane;
+}
+
+}  // namespace dbm
+
+namespace dbm {
+
+template <int S>
+void fill_f64_consts(const dbm_handle *h, F64Consts<S> &c)
+{
+    memset(&c, 0, sizeof(c));
+    const dbm_params &p = h->p;
+    for (int s = 0; s < S; ++s) {
+        const dbm_species &sp = p.sp[s];
+        for (int i = 0; i < Q; ++i) {
+            for (int k = 0; k < Q; ++k) c.cinv[s][i][k] = h->cinv[s][i][k];
+            const double x = dir_x(i) * sp.v[i >> 2], y = dir_y(i) * sp.v[i >> 2], e = sp.eta[i >> 2];
+            c.vx[s][i] = x;
+            c.vy[s][i] = y;
+            c.q[s][i] = x * x + y * y + e * e;  // host code is built without contraction
+        }
+        c.m[s] = sp.m;
+        c.I[s] = sp.I;
+        c.tau[s] = sp.tau;
+        c.a[s] = sp.a_stoich;
+    }
+    c.dt = p.dt;
+    c.dx = p.dx;
+    c.dy = p.dy;
+    c.ax = p.accel[0];
+    c.ay = p.accel[1];
+    c.k_ov = p.k_ov;
+    c.Ea_over_R = p.Ea_over_R;
+    c.Qheat = p.Q;
+    c.fuel = p.fuel;
+    c.oxid = p.oxidizer;
+    c.has_reaction = p.k_ov != 0.0;
+    c.has_force = p.accel[0] != 0.0 || p.accel[1] != 0.0;
     c.nx = p.nx;
     c.ny = p.ny;
     c.pitch = h->lay.pitch;

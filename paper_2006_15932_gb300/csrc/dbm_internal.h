@@ -44,7 +44,11 @@ struct StepConsts {
     real q4[S][4];       // 4 (v.v + eta^2): energy of a unit ring mean
     real wv[S][4];       // 2 v_r (axis) or 4 v_r (diagonal): momentum of a unit vector part
     real cdx[S][4], cdy[S][4];  // v_r dt/dx, v_r dt/dy
-    real mt[S], dpi_tau[S], dpi[S], inv_m[S], tau[S], dt_tau[S];
+    // mixture weights as hi + lo pairs of the exact products of the constants
+    // the kernel applies: lam = m dt_tau (momentum/energy weight of a species
+    // in an update), kap = lam dpi inv_m (its heat capacity weight)
+    real lam_h[S], lam_l[S], kap_h[S], kap_l[S];
+    real dpi[S], inv_m[S], tau[S], dt_tau[S];
     real accel_x, accel_y;
     double tau_d[S], tau_a[S];  // tau^s, tau^s a^s
     double k_ov, Ea_over_R, Qheat, src;  // src = sum_s (D+I^s) a^s
@@ -105,5 +109,28 @@ template <int S>
 void fill_out_consts(const dbm_handle *h, OutConsts<S> &c);
 
 int set_cuda_error(dbm_handle *h, cudaError_t e, const char *what);
+
+}  // namespace dbm
+
+namespace dbm {
+
+// Kernel parameters of the FP64 reference-order step (dbm_step_f64.cu):
+// per-velocity constants so that every product is formed as in the
+// plain restatement of the paper (same operands, same order).
+template <int S>
+struct F64Consts {
+    double cinv[S][Q][Q];
+    double vx[S][Q], vy[S][Q], q[S][Q];  // q = vx*vx + vy*vy + eta*eta
+    double m[S], I[S], tau[S], a[S];
+    double dt, dx, dy, ax, ay;
+    double k_ov, Ea_over_R, Qheat;
+    int fuel, oxid, has_reaction, has_force;
+    int nx, ny, pitch, bc_x, bc_y;
+    long long plane;
+};
+
+template <int S>
+void fill_f64_consts(const dbm_handle *h, F64Consts<S> &c);
+int launch_step_f64(dbm_handle *h, int cur, cudaStream_t st);
 
 }  // namespace dbm

@@ -220,17 +220,14 @@ __device__ __forceinline__ void store_images(real *pl, int x, int y, int nx, int
 }
 
 // Mixture temperature T = (W - (u.u) w) / wd of one cell, with the
-// cancelling subtraction in FP64.
-template <typename real>
-__device__ __forceinline__ real mixture_T(real W, real w, real wd, real ux, real uy, double &Td)
+// cancelling subtraction in FP64 (W = sum lam E, w = sum lam n,
+// wd = sum kap n: the weights under which the update conserves momentum and
+// energy exactly).
+__device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux, float uy, double &Td)
 {
-    if (sizeof(real) == 8) {
-        Td = ((double)W - ((double)ux * (double)ux + (double)uy * (double)uy) * (double)w) / (double)wd;
-        return (real)Td;
-    }
-    const real u2 = ux * ux + uy * uy;
+    const float u2 = ux * ux + uy * uy;
     const double num = (double)W - (double)u2 * (double)w;
-    const real T = (real)num * (real(1) / wd);
+    const float T = (float)num / wd;
     Td = (double)T;
     return T;
 }
@@ -276,17 +273,17 @@ __device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Ti
         }
         n0[s] = sn0;
         n1[s] = sn1;
-        const real mt = c.mt[s];  // m / tau
-        w0 += mt * sn0;
-        w1 += mt * sn1;
-        wx0 += mt * sx0;
-        wx1 += mt * sx1;
-        wy0 += mt * sy0;
-        wy1 += mt * sy1;
-        we0 += mt * se0;
-        we1 += mt * se1;
-        wd0 += c.dpi_tau[s] * sn0;
-        wd1 += c.dpi_tau[s] * sn1;
+        const real lh = c.lam_h[s], ll = c.lam_l[s], kh = c.kap_h[s], kl = c.kap_l[s];
+        w0 += lh * sn0 + ll * sn0;
+        w1 += lh * sn1 + ll * sn1;
+        wx0 += lh * sx0 + ll * sx0;
+        wx1 += lh * sx1 + ll * sx1;
+        wy0 += lh * sy0 + ll * sy0;
+        wy1 += lh * sy1 + ll * sy1;
+        we0 += lh * se0 + ll * se0;
+        we1 += lh * se1 + ll * se1;
+        wd0 += kh * sn0 + kl * sn0;
+        wd1 += kh * sn1 + kl * sn1;
         cap0 += c.dpi[s] * sn0;
         cap1 += c.dpi[s] * sn1;
     }
@@ -294,8 +291,8 @@ __device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Ti
     // 2. mixture velocity and temperature
     const real ux0 = wx0 / w0, uy0 = wy0 / w0, ux1 = wx1 / w1, uy1 = wy1 / w1;
     double T0d, T1d;
-    const real T0 = mixture_T<real>(we0, w0, wd0, ux0, uy0, T0d);
-    const real T1 = mixture_T<real>(we1, w1, wd1, ux1, uy1, T1d);
+    const real T0 = mixture_T(we0, w0, wd0, ux0, uy0, T0d);
+    const real T1 = mixture_T(we1, w1, wd1, ux1, uy1, T1d);
 
     unsigned bad = 0;
     real a0 = 0, a1 = 0;  // sum_s |n^s| of both cells
@@ -444,7 +441,7 @@ __device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Ti
 
 // Generic kernel: inputs from global memory through the read-only path.
 template <typename real, int S>
-__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(256, 2)
     k_step(const __grid_constant__ StepConsts<real, S> c, const real *__restrict__ fin,
            real *__restrict__ fout, unsigned *__restrict__ flag)
 {
