@@ -202,6 +202,35 @@ int dbm_nonequilibrium(dbm_handle *h, double *out, void *stream);
  * Uses the bound scratch buffer.  Async on stream. */
 int dbm_conservation(dbm_handle *h, double *out, void *stream);
 
+/* Capacity, in doubles, of the library's own device array that holds the
+ * reduction partials of dbm_conservation_noalloc (32 KB on every GPU that
+ * loads the library, kept until the process exits). */
+#define DBM_NOALLOC_SCRATCH_DOUBLES 4096
+
+/* The totals of dbm_conservation without any caller-provided scratch
+ * buffer.  The paper has no counterpart to this entry point: it is for
+ * callers that cannot allocate device memory when they need the totals --
+ * for example a plug-in running inside a host application that owns all of
+ * the GPU's memory and allows no further allocation -- and so cannot hand
+ * the library a scratch buffer.
+ *   state  a state buffer in this handle's layout (device memory), or NULL
+ *          for the handle's current bound state;
+ *   out    S+4 doubles, laid out as for dbm_conservation (device or
+ *          addressable host memory).
+ * The result equals dbm_conservation's (same reduction blocks and order).
+ * The block partials go to a static device array of
+ * DBM_NOALLOC_SCRATCH_DOUBLES doubles inside the library instead of the
+ * scratch buffer; a problem whose partials do not fit (more than 4 species)
+ * is rejected with DBM_ERR_INVALID.  The call makes no cudaMalloc, cudaFree
+ * or other allocation.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current: make that
+ * first call before any stream capture, and call with the device that holds
+ * `state` current.  All calls on a device share the one array, and each
+ * call overwrites every partial it reads (nothing needs clearing), so calls
+ * that may overlap on the GPU race with each other: order them on one
+ * stream or synchronise between them.  Async on stream. */
+int dbm_conservation_noalloc(dbm_handle *h, const void *state, double *out, void *stream);
+
 /* Synchronise the stream, read the sticky device health flag and map it to
  * DBM_OK, DBM_ERR_NEGATIVE or DBM_ERR_NONFINITE.  *bits (may be NULL)
  * receives the raw dbm_health_bits. */

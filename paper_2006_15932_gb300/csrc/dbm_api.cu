@@ -541,6 +541,23 @@ int dbm_conservation(dbm_handle *h, double *out, void *stream)
     return launch_conservation(h, h->f[h->cur], out, (cudaStream_t)stream);
 }
 
+int dbm_conservation_noalloc(dbm_handle *h, const void *state, double *out, void *stream)
+{
+    if (!h) return DBM_ERR_INVALID;
+    if (!out) return fail(h, DBM_ERR_INVALID, "conservation_noalloc: null out");
+    if (!state) {
+        if (!h->bound) return fail(h, DBM_ERR_UNBOUND, "conservation_noalloc: no state given and none bound");
+        state = h->f[h->cur];
+    }
+    const size_t need = (size_t)CONS_BLOCKS * (h->p.nspecies + 4);
+    if (need > DBM_NOALLOC_SCRATCH_DOUBLES)
+        return fail(h, DBM_ERR_INVALID,
+                    "conservation_noalloc: its static scratch holds %d doubles, %d species need %zu "
+                    "(use dbm_conservation with a scratch buffer)",
+                    DBM_NOALLOC_SCRATCH_DOUBLES, h->p.nspecies, need);
+    return launch_conservation_noalloc(h, state, out, (cudaStream_t)stream);
+}
+
 int dbm_status(dbm_handle *h, void *stream, unsigned *bits)
 {
     int rc = check_bound(h);

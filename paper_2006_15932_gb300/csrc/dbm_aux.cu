@@ -2,6 +2,8 @@
 // of the D2V16 DBM: f = f^eq from macroscopic fields, checkpoint load/read,
 // the macroscopic fields, the nonequilibrium moments (Eqs. Delta2, Delta31,
 // Delta3, Delta42) and the conserved totals.
+#include <mutex>
+
 #include "dbm_consts.h"
 #include "dbm_device.cuh"
 
@@ -400,6 +402,72 @@ int launch_conservation(dbm_handle *h, const void *f, double *out, cudaStream_t 
         return DBM_ERR_INVALID;
     }
     return set_cuda_error(h, cudaGetLastError(), "conservation kernel launch");
+}
+
+// ---------------------------------------------------------------------------
+// Conserved totals without a caller-provided scratch buffer.
+//
+// Some callers cannot allocate device memory at the point where they need
+// the totals (for example a plug-in that runs inside a host application
+// which owns all of the GPU's memory and forbids further allocations).  For
+// them the block partials of the reduction live in this file-scope device
+// array instead of the caller's scratch buffer.  Every GPU that loads the
+// library holds the array until the process exits.  Host code must not
+// pass the array's name to a kernel (on the host it is only a stand-in):
+// its device address is looked up once per device with cudaGetSymbolAddress
+// and cached.
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) double g_noalloc_partials[DBM_NOALLOC_SCRATCH_DOUBLES];
+
+static const int NOALLOC_MAX_DEVICES = 64;
+static double *g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+// Device address of g_noalloc_partials on the current device (looked up on
+// the first call per device, with that device current).
+static int noalloc_scratch(dbm_handle *h, double **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_cuda_error(h, e, "conservation_noalloc: current device");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return DBM_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+        if (e != cudaSuccess) return set_cuda_error(h, e, "conservation_noalloc: cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = (double *)ptr;
+    }
+    *out = g_noalloc_addr[dev];
+    return DBM_OK;
+}
+
+template <typename real, int S>
+static void cons_noalloc_t(dbm_handle *h, const void *f, double *partial, double *out, cudaStream_t st)
+{
+    OutConsts<S> c;
+    fill_out_consts<S>(h, c);
+    k_cons_partial<real, S><<<CONS_BLOCKS, 256, 0, st>>>(c, (const real *)f, partial);
+    k_cons_final<<<1, 32, 0, st>>>(partial, CONS_BLOCKS, S + 4, out);
+}
+
+int launch_conservation_noalloc(dbm_handle *h, const void *f, double *out, cudaStream_t st)
+{
+    const size_t need = (size_t)CONS_BLOCKS * (h->p.nspecies + 4);
+    if (need > DBM_NOALLOC_SCRATCH_DOUBLES) return DBM_ERR_INVALID;
+    double *partial = nullptr;
+    int rc = noalloc_scratch(h, &partial);
+    if (rc) return rc;
+    // every block overwrites all of its partials, so nothing needs clearing
+    if (h->p.precision == DBM_FP64) {
+        DBM_DISPATCH_S(h->p.nspecies, (cons_noalloc_t<double, S>(h, f, partial, out, st)));
+    } else if (h->p.precision == DBM_FP32) {
+        DBM_DISPATCH_S(h->p.nspecies, (cons_noalloc_t<float, S>(h, f, partial, out, st)));
+    } else {
+        return DBM_ERR_INVALID;
+    }
+    return set_cuda_error(h, cudaGetLastError(), "conservation_noalloc kernel launch");
 }
 
 }  // namespace dbm

@@ -102,6 +102,7 @@ int launch_get_f(dbm_handle *h, const void *f, double *dst, cudaStream_t st);
 int launch_moments(dbm_handle *h, const void *f, double *out, cudaStream_t st);
 int launch_noneq(dbm_handle *h, const void *f, double *out, cudaStream_t st);
 int launch_conservation(dbm_handle *h, const void *f, double *out, cudaStream_t st);
+int launch_conservation_noalloc(dbm_handle *h, const void *f, double *out, cudaStream_t st);
 
 template <typename real, int S>
 void fill_step_consts(const dbm_handle *h, StepConsts<real, S> &c);

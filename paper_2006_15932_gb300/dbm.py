@@ -38,7 +38,7 @@ KERNELS = {"auto": 0, "generic": 1, "tma": 2}
 EXPORTS = [
     "dbm_init", "dbm_init_error", "dbm_equilibrium_matrix", "dbm_get_layout", "dbm_state_bytes", "dbm_scratch_bytes",
     "dbm_bind", "dbm_set_state", "dbm_set_f", "dbm_get_f", "dbm_step", "dbm_moments",
-    "dbm_nonequilibrium", "dbm_conservation", "dbm_status", "dbm_steps_taken",
+    "dbm_nonequilibrium", "dbm_conservation", "dbm_conservation_noalloc", "dbm_status", "dbm_steps_taken",
     "dbm_last_error", "dbm_destroy",
 ]
 
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
     L.dbm_moments.argtypes = [H, vp, vp]
     L.dbm_nonequilibrium.argtypes = [H, vp, vp]
     L.dbm_conservation.argtypes = [H, vp, vp]
+    L.dbm_conservation_noalloc.argtypes = [H, vp, vp, vp]
     L.dbm_status.argtypes = [H, vp, C.POINTER(C.c_uint)]
     L.dbm_steps_taken.argtypes = [H]
     L.dbm_steps_taken.restype = C.c_longlong
@@ -239,6 +240,12 @@ def dbm_nonequilibrium(h, out: int, stream: int = 0) -> None:
 
 def dbm_conservation(h, out: int, stream: int = 0) -> None:
     _check(h, load().dbm_conservation(h, out, stream))
+
+
+def dbm_conservation_noalloc(h, state: int, out: int, stream: int = 0) -> None:
+    """Conserved totals without a scratch buffer (see include/dbm.h);
+    state = 0 means the handle's current bound state."""
+    _check(h, load().dbm_conservation_noalloc(h, state or None, out, stream))
 
 
 def dbm_status(h, stream: int = 0) -> tuple[int, int]:
