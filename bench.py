@@ -93,6 +93,15 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
+def step_kernel_name(pb, precision):
+    """The step kernel dbm_step dispatches for this problem (DBM_KERNEL_AUTO)."""
+    if precision == "fp64":
+        return f"k_step_f64<{pb.ns}>"
+    if pb.ns <= 3:
+        return f"k_step_tma<float,{pb.ns},{64 if pb.ns <= 2 else 32},8>"
+    return f"k_step<float,{pb.ns}>"
+
+
 def ncu_traffic(name, precision):
     """DRAM bytes per launch of the step kernel from the committed ncu
     summary, or None when the kernel source changed since the capture."""
@@ -307,7 +316,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": f"k_step<{'float' if args.precision == 'fp32' else 'double'},{pb.ns}>",
+                "kernel": step_kernel_name(pb, args.precision),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "median_launch_ms": statistics.median(per_launch)}
 
