@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="kh4096", choices=["kh4096", "reactive", "sod"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and e2e side legs")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--grid", default=None, help="override the grid, e.g. 2048x1024 (profiling runs)")
@@ -69,10 +69,19 @@ def workload_config(pb, name, precision):
         "precision": precision,
         "reactive": pb.k_ov != 0.0,
         "boundary": ["periodic" if b == 0 else "outflow" for b in (pb.bc_x, pb.bc_y)],
-        "state_bytes_per_buffer": pb.nx * pb.ny * pb.ns * 16 * (8 if precision == "fp64" else 4),
+        "state_bytes_per_buffer": int(pb.nx * pb.ny * pb.ns * 16 * bytes_per_update(precision, pb.ns) / 32),
         "l2_policy": "inputs larger than L2" if pb.nx * pb.ny * pb.ns * 64 > 129e6
         else "state fits in L2 (no flush)",
     }
+
+
+def bytes_per_update(precision, ns):
+    """Algorithmic HBM bytes per species-cell update: the 16 stored values
+    read and written; BF16DEV adds the cell's S+3 float moments (read and
+    written) shared by its S species."""
+    if precision == "bf16dev":
+        return 16 * 2 * 2 + 2 * (ns + 3) * 4 / ns
+    return BYTES_PER_UPDATE[precision]
 
 
 def measured_peaks():
@@ -97,6 +106,8 @@ def step_kernel_name(pb, precision):
     """The step kernel dbm_step dispatches for this problem (DBM_KERNEL_AUTO)."""
     if precision == "fp64":
         return f"k_step_f64<{pb.ns}>"
+    if precision == "bf16dev":
+        return f"k_step_bf16<{pb.ns},64,8>"
     if pb.ns <= 3:
         return f"k_step_tma<float,{pb.ns},{64 if pb.ns <= 2 else 32},8>"
     return f"k_step<float,{pb.ns}>"
@@ -308,7 +319,7 @@ def main():
     value = updates_per_rank * world / (ms_max * 1e-3)
 
     peak, peak_kind = measured_peaks()
-    bpu = BYTES_PER_UPDATE[args.precision]
+    bpu = bytes_per_update(args.precision, pb.ns)
     avg_launch_ms = statistics.mean(per_launch)
     bytes_per_launch = pb.nx * pb.ny * pb.ns * bpu
     achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
@@ -328,7 +339,8 @@ def main():
             extras["fp64"] = measure_fp64(D, pb, dev, stream)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16dev": "bf16+f32"}[args.precision],
             "data": "synthetic (seeded analytic initial fields)", "config": cfg, "roofline": roofline,
             "clocks": clk, "gpu_launches": K, "e2e": e2e}
     line.update(extras)

@@ -262,6 +262,11 @@ static int validate(dbm_handle *h, const dbm_params &p)
         return fail(h, DBM_ERR_INVALID, "unknown precision %d", p.precision);
     if (p.step_kernel < DBM_KERNEL_AUTO || p.step_kernel > DBM_KERNEL_TMA)
         return fail(h, DBM_ERR_INVALID, "unknown step kernel %d", p.step_kernel);
+    if (p.precision == DBM_BF16DEV &&
+        (p.nspecies > 4 || p.k_ov != 0.0 || p.accel[0] != 0.0 || p.accel[1] != 0.0 || p.step_kernel == DBM_KERNEL_TMA))
+        return fail(h, DBM_ERR_INVALID,
+                    "BF16DEV storage is built for up to 4 species without reaction or force "
+                    "(its reference equilibrium is that of the stored moments)");
     if (!isfinite(p.accel[0]) || !isfinite(p.accel[1]))
         return fail(h, DBM_ERR_INVALID, "acceleration must be finite");
     double vmax = 0.0;
@@ -475,7 +480,6 @@ int dbm_set_state(dbm_handle *h, const double *rho_s, const double *ux, const do
     cudaStream_t st = (cudaStream_t)stream;
     rc = set_cuda_error(h, cudaMemsetAsync(h->scratch, 0, SCRATCH_HEAD, st), "clear health flag");
     if (rc) return rc;
-    if (h->p.precision == DBM_BF16DEV) return fail(h, DBM_ERR_INVALID, "BF16DEV not built yet");
     rc = launch_set_state(h, h->f[h->cur], rho_s, ux, uy, T, st);
     if (rc == DBM_OK) h->steps = 0;
     return rc;

@@ -4,8 +4,7 @@
 // Delta3, Delta42) and the conserved totals.
 #include <mutex>
 
-#include "dbm_consts.h"
-#include "dbm_device.cuh"
+#include "dbm_bf16.cuh"
 
 namespace dbm {
 
@@ -67,17 +66,32 @@ __global__ void __launch_bounds__(256)
     for (int p = 0; p < nplanes; ++p) dst[p * N + d] = (double)f[p * plane + cell];
 }
 
+// Source of f for the output kernels: a plain FP64 or FP32 state buffer
+// (the BF16-deviation state has BfSrc, which rebuilds f).
+template <typename real>
+struct PlainSrc {
+    const real *f;
+    long long plane;
+    __device__ __forceinline__ void load16(int s, long long cell, double v[Q]) const
+    {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v[i] = (double)f[(s * Q + i) * plane + cell];
+    }
+};
+
 // Species moments of one cell in FP64: n, j = sum f v, E = sum f (v.v+eta^2).
-template <typename real, int S>
-__device__ __forceinline__ void cell_moments(const OutConsts<S> &c, const real *f, long long cell,
+template <int S, class Src>
+__device__ __forceinline__ void cell_moments(const OutConsts<S> &c, const Src &src, long long cell,
                                              double n[S], double jx[S], double jy[S], double en[S])
 {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         double sn = 0, sx = 0, sy = 0, se = 0;
+        double fv[Q];
+        src.load16(s, cell, fv);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const double v = (double)f[(s * Q + i) * c.plane + cell];
+            const double v = fv[i];
             const int r = i >> 2;
             sn += v;
             sx += dir_x(i) * c.vr[s][r] * v;
@@ -115,9 +129,9 @@ __device__ __forceinline__ void cell_mixture(const OutConsts<S> &c, const double
     T = num / den;
 }
 
-template <typename real, int S>
+template <int S, class Src>
 __global__ void __launch_bounds__(256)
-    k_moments(const __grid_constant__ OutConsts<S> c, const real *__restrict__ f,
+    k_moments(const __grid_constant__ OutConsts<S> c, const __grid_constant__ Src src,
               double *__restrict__ out)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,7 +141,7 @@ __global__ void __launch_bounds__(256)
     const long long d = (long long)y * c.nx + x;
     const long long cell = (long long)(y + GY) * c.pitch + (x + GX);
     double n[S], jx[S], jy[S], en[S];
-    cell_moments<real, S>(c, f, cell, n, jx, jy, en);
+    cell_moments<S>(c, src, cell, n, jx, jy, en);
     double rho = 0, ntot = 0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -151,9 +165,9 @@ __global__ void __launch_bounds__(256)
     out[(4 * S + 4) * N + d] = ntot * T;
 }
 
-template <typename real, int S>
+template <int S, class Src>
 __global__ void __launch_bounds__(128)
-    k_noneq(const __grid_constant__ OutConsts<S> c, const real *__restrict__ f,
+    k_noneq(const __grid_constant__ OutConsts<S> c, const __grid_constant__ Src src,
             double *__restrict__ out)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -163,7 +177,7 @@ __global__ void __launch_bounds__(128)
     const long long d = (long long)y * c.nx + x;
     const long long cell = (long long)(y + GY) * c.pitch + (x + GX);
     double n[S], jx[S], jy[S], en[S];
-    cell_moments<real, S>(c, f, cell, n, jx, jy, en);
+    cell_moments<S>(c, src, cell, n, jx, jy, en);
     double ux, uy, T;
     cell_mixture<S>(c, n, jx, jy, en, ux, uy, T);
 #pragma unroll 1
@@ -174,6 +188,8 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
         for (int k = 0; k < 20; ++k) acc[k] = 0.0;
         const double m = c.m[s];
+        double fc[Q];
+        src.load16(s, cell, fc);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             double feq = 0.0;
@@ -182,7 +198,7 @@ __global__ void __launch_bounds__(128)
             const int r = i >> 2;
             const double vx = dir_x(i) * c.vr[s][r], vy = dir_y(i) * c.vr[s][r];
             const double q = c.qr[s][r];
-            const double fv = (double)f[(s * Q + i) * c.plane + cell];
+            const double fv = fc[i];
             const double dm = m * (fv - feq), mf = 0.5 * m * fv, me = 0.5 * m * feq;
             acc[0] += dm * vx * vx;
             acc[1] += dm * vx * vy;
@@ -213,9 +229,9 @@ __global__ void __launch_bounds__(128)
 // Conserved totals: each block sums a fixed, strided subset of cells in a
 // fixed order and reduces them by a fixed tree; the final kernel adds the
 // block partials in block order.  The result is independent of timing.
-template <typename real, int S>
+template <int S, class Src>
 __global__ void __launch_bounds__(256)
-    k_cons_partial(const __grid_constant__ OutConsts<S> c, const real *__restrict__ f,
+    k_cons_partial(const __grid_constant__ OutConsts<S> c, const __grid_constant__ Src src,
                    double *__restrict__ partial)
 {
     constexpr int K = S + 4;
@@ -231,9 +247,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const double m = c.m[s];
+            double fv[Q];
+            src.load16(s, cell, fv);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const double v = (double)f[(s * Q + i) * c.plane + cell];
+                const double v = fv[i];
                 const int r = i >> 2;
                 acc[s] += m * v;
                 acc[S] += m * v * (dir_x(i) * c.vr[s][r]);
@@ -287,6 +305,15 @@ static dim3 cell_grid(const dbm_handle *h, dim3 block)
     default: return DBM_ERR_INVALID;         \
     }
 
+#define DBM_DISPATCH_BF(S_, CALL)            \
+    switch (S_) {                            \
+    case 1: { constexpr int S = 1; CALL; } break; \
+    case 2: { constexpr int S = 2; CALL; } break; \
+    case 3: { constexpr int S = 3; CALL; } break; \
+    case 4: { constexpr int S = 4; CALL; } break; \
+    default: return DBM_ERR_INVALID;         \
+    }
+
 template <typename real, int S>
 static void set_state_t(dbm_handle *h, void *f, const double *rho_s, const double *ux,
                         const double *uy, const double *T, cudaStream_t st)
@@ -305,7 +332,7 @@ int launch_set_state(dbm_handle *h, void *f, const double *rho_s, const double *
     } else if (h->p.precision == DBM_FP32) {
         DBM_DISPATCH_S(h->p.nspecies, (set_state_t<float, S>(h, f, rho_s, ux, uy, T, st)));
     } else {
-        return DBM_ERR_INVALID;
+        return launch_set_state_bf16(h, f, rho_s, ux, uy, T, st);
     }
     return set_cuda_error(h, cudaGetLastError(), "set_state kernel launch");
 }
@@ -321,7 +348,7 @@ int launch_set_f(dbm_handle *h, void *f, const double *src, cudaStream_t st)
         k_set_f<float><<<cell_grid(h, b), b, 0, st>>>((float *)f, src, np, h->p.nx, h->p.ny,
                                                       h->lay.pitch, h->lay.plane, h->p.bc_x, h->p.bc_y);
     else
-        return DBM_ERR_INVALID;
+        return launch_set_f_bf16(h, f, src, st);
     return set_cuda_error(h, cudaGetLastError(), "set_f kernel launch");
 }
 
@@ -336,71 +363,94 @@ int launch_get_f(dbm_handle *h, const void *f, double *dst, cudaStream_t st)
         k_get_f<float><<<cell_grid(h, b), b, 0, st>>>((const float *)f, dst, np, h->p.nx, h->p.ny,
                                                       h->lay.pitch, h->lay.plane);
     else
-        return DBM_ERR_INVALID;
+        return launch_get_f_bf16(h, f, dst, st);
     return set_cuda_error(h, cudaGetLastError(), "get_f kernel launch");
 }
 
+// The source of f for a state buffer of this handle's precision.
 template <typename real, int S>
-static void moments_t(dbm_handle *h, const void *f, double *out, cudaStream_t st)
+static PlainSrc<real> plain_src(const dbm_handle *h, const void *f)
+{
+    return PlainSrc<real>{(const real *)f, h->lay.plane};
+}
+template <int S>
+static BfSrc<S> bf_src(const dbm_handle *h, const void *f)
+{
+    BfSrc<S> b;
+    fill_step_consts<float, S>(h, b.k);
+    b.st = bf_state(h, (void *)f);
+    return b;
+}
+
+template <int S, class Src>
+static void moments_t(dbm_handle *h, const Src &src, double *out, cudaStream_t st)
 {
     OutConsts<S> c;
     fill_out_consts<S>(h, c);
     dim3 b(32, 8);
-    k_moments<real, S><<<cell_grid(h, b), b, 0, st>>>(c, (const real *)f, out);
+    k_moments<S, Src><<<cell_grid(h, b), b, 0, st>>>(c, src, out);
 }
 
 int launch_moments(dbm_handle *h, const void *f, double *out, cudaStream_t st)
 {
     if (h->p.precision == DBM_FP64) {
-        DBM_DISPATCH_S(h->p.nspecies, (moments_t<double, S>(h, f, out, st)));
+        DBM_DISPATCH_S(h->p.nspecies, (moments_t<S>(h, plain_src<double, S>(h, f), out, st)));
     } else if (h->p.precision == DBM_FP32) {
-        DBM_DISPATCH_S(h->p.nspecies, (moments_t<float, S>(h, f, out, st)));
+        DBM_DISPATCH_S(h->p.nspecies, (moments_t<S>(h, plain_src<float, S>(h, f), out, st)));
     } else {
-        return DBM_ERR_INVALID;
+        DBM_DISPATCH_BF(h->p.nspecies, (moments_t<S>(h, bf_src<S>(h, f), out, st)));
     }
     return set_cuda_error(h, cudaGetLastError(), "moments kernel launch");
 }
 
-template <typename real, int S>
-static void noneq_t(dbm_handle *h, const void *f, double *out, cudaStream_t st)
+template <int S, class Src>
+static void noneq_t(dbm_handle *h, const Src &src, double *out, cudaStream_t st)
 {
     OutConsts<S> c;
     fill_out_consts<S>(h, c);
     dim3 b(32, 4);
-    k_noneq<real, S><<<cell_grid(h, b), b, 0, st>>>(c, (const real *)f, out);
+    k_noneq<S, Src><<<cell_grid(h, b), b, 0, st>>>(c, src, out);
 }
 
 int launch_noneq(dbm_handle *h, const void *f, double *out, cudaStream_t st)
 {
     if (h->p.precision == DBM_FP64) {
-        DBM_DISPATCH_S(h->p.nspecies, (noneq_t<double, S>(h, f, out, st)));
+        DBM_DISPATCH_S(h->p.nspecies, (noneq_t<S>(h, plain_src<double, S>(h, f), out, st)));
     } else if (h->p.precision == DBM_FP32) {
-        DBM_DISPATCH_S(h->p.nspecies, (noneq_t<float, S>(h, f, out, st)));
+        DBM_DISPATCH_S(h->p.nspecies, (noneq_t<S>(h, plain_src<float, S>(h, f), out, st)));
     } else {
-        return DBM_ERR_INVALID;
+        DBM_DISPATCH_BF(h->p.nspecies, (noneq_t<S>(h, bf_src<S>(h, f), out, st)));
     }
     return set_cuda_error(h, cudaGetLastError(), "nonequilibrium kernel launch");
 }
 
-template <typename real, int S>
-static void cons_t(dbm_handle *h, const void *f, double *out, cudaStream_t st)
+template <int S, class Src>
+static void cons_t(dbm_handle *h, const Src &src, double *partial, double *out, cudaStream_t st)
 {
     OutConsts<S> c;
     fill_out_consts<S>(h, c);
-    double *partial = (double *)((char *)h->scratch + SCRATCH_HEAD);
-    k_cons_partial<real, S><<<CONS_BLOCKS, 256, 0, st>>>(c, (const real *)f, partial);
+    k_cons_partial<S, Src><<<CONS_BLOCKS, 256, 0, st>>>(c, src, partial);
     k_cons_final<<<1, 32, 0, st>>>(partial, CONS_BLOCKS, S + 4, out);
+}
+
+// Conserved totals into `out` with the block partials in `partial`.
+static int conservation_into(dbm_handle *h, const void *f, double *partial, double *out, cudaStream_t st)
+{
+    if (h->p.precision == DBM_FP64) {
+        DBM_DISPATCH_S(h->p.nspecies, (cons_t<S>(h, plain_src<double, S>(h, f), partial, out, st)));
+    } else if (h->p.precision == DBM_FP32) {
+        DBM_DISPATCH_S(h->p.nspecies, (cons_t<S>(h, plain_src<float, S>(h, f), partial, out, st)));
+    } else {
+        DBM_DISPATCH_BF(h->p.nspecies, (cons_t<S>(h, bf_src<S>(h, f), partial, out, st)));
+    }
+    return DBM_OK;
 }
 
 int launch_conservation(dbm_handle *h, const void *f, double *out, cudaStream_t st)
 {
-    if (h->p.precision == DBM_FP64) {
-        DBM_DISPATCH_S(h->p.nspecies, (cons_t<double, S>(h, f, out, st)));
-    } else if (h->p.precision == DBM_FP32) {
-        DBM_DISPATCH_S(h->p.nspecies, (cons_t<float, S>(h, f, out, st)));
-    } else {
-        return DBM_ERR_INVALID;
-    }
+    double *partial = (double *)((char *)h->scratch + SCRATCH_HEAD);
+    const int rc = conservation_into(h, f, partial, out, st);
+    if (rc) return rc;
     return set_cuda_error(h, cudaGetLastError(), "conservation kernel launch");
 }
 
@@ -443,15 +493,6 @@ static int noalloc_scratch(dbm_handle *h, double **out)
     return DBM_OK;
 }
 
-template <typename real, int S>
-static void cons_noalloc_t(dbm_handle *h, const void *f, double *partial, double *out, cudaStream_t st)
-{
-    OutConsts<S> c;
-    fill_out_consts<S>(h, c);
-    k_cons_partial<real, S><<<CONS_BLOCKS, 256, 0, st>>>(c, (const real *)f, partial);
-    k_cons_final<<<1, 32, 0, st>>>(partial, CONS_BLOCKS, S + 4, out);
-}
-
 int launch_conservation_noalloc(dbm_handle *h, const void *f, double *out, cudaStream_t st)
 {
     const size_t need = (size_t)CONS_BLOCKS * (h->p.nspecies + 4);
@@ -460,13 +501,8 @@ int launch_conservation_noalloc(dbm_handle *h, const void *f, double *out, cudaS
     int rc = noalloc_scratch(h, &partial);
     if (rc) return rc;
     // every block overwrites all of its partials, so nothing needs clearing
-    if (h->p.precision == DBM_FP64) {
-        DBM_DISPATCH_S(h->p.nspecies, (cons_noalloc_t<double, S>(h, f, partial, out, st)));
-    } else if (h->p.precision == DBM_FP32) {
-        DBM_DISPATCH_S(h->p.nspecies, (cons_noalloc_t<float, S>(h, f, partial, out, st)));
-    } else {
-        return DBM_ERR_INVALID;
-    }
+    rc = conservation_into(h, f, partial, out, st);
+    if (rc) return rc;
     return set_cuda_error(h, cudaGetLastError(), "conservation_noalloc kernel launch");
 }
 

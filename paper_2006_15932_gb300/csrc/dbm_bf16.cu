@@ -1,0 +1,261 @@
+// dbm_bf16.cu -- the step and the state transfers of the BF16-deviation
+// storage (see dbm_bf16.cuh).
+//
+// One CTA steps a TX x TY tile.  Phase A rebuilds f (FP32) of the tile and
+// its radius-2 halo in shared memory from the stored moments and bfloat16
+// deviations; phase B runs the same per-pair FP32 arithmetic as the FP32
+// kernels (step_pair) on that tile and stores delta^{n+1} and the
+// reference moments.  Reactions and forces are not supported in this
+// storage (their equilibrium is not the one of the stored moments); init
+// rejects them.
+#include "dbm_bf16.cuh"
+
+namespace dbm {
+
+template <int S, int TX, int TY>
+__global__ void __launch_bounds__((TX / 2) * TY, 2)
+    k_step_bf16(const __grid_constant__ StepConsts<float, S> c, BfState in, BfState out,
+                unsigned *__restrict__ flag)
+{
+    constexpr int BX = TX + 4, BY = TY + 4, NP = S * Q, NPAIR = BX / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tile = reinterpret_cast<float *>(smem_raw);  // [NP][BY][BX], column 0 = x0 - 2
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nthr = (TX / 2) * TY, tid = ty * (TX / 2) + tx;
+    const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
+
+    // phase A: rebuild f for the tile and its halo, pairs of cells
+    for (int k = tid; k < NPAIR * BY; k += nthr) {
+        const int rr = k / NPAIR, pc = k % NPAIR;
+        const int x = bx0 - 2 + 2 * pc, y = by0 - 2 + rr;
+        const bool ok0 = x <= c.nx + 1 && y <= c.ny + 1;  // inside the ghost band
+        const bool ok1 = x + 1 <= c.nx + 1 && ok0;
+        const long long cell = (long long)(y + GY) * c.pitch + (x + GX);
+        float *dst = tile + rr * BX + 2 * pc;
+#pragma unroll 1
+        for (int s = 0; s < S; ++s) {
+            float f0[Q], f1[Q];
+            if (ok0) bf_cell_f<S>(c, in, s, cell, f0);
+            if (ok1) bf_cell_f<S>(c, in, s, cell + 1, f1);
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+                *reinterpret_cast<float2 *>(dst + (s * Q + i) * (BY * BX)) =
+                    make_float2(ok0 ? f0[i] : 0.0f, ok1 ? f1[i] : 0.0f);
+        }
+    }
+    __syncthreads();
+
+    // phase B: the step from shared memory
+    const int x0 = bx0 + 2 * tx, y = by0 + ty;
+    if (x0 >= c.nx || y >= c.ny) return;
+    SmemTile<float> t;
+    t.base = tile + (ty + 2) * BX + (2 * tx + 2);
+    t.P = BY * BX;
+    t.py = BX;
+    BfOut o{out, c.nx, c.ny, c.pitch, S};
+    step_pair<float, S>(c, t, x0, y, o, flag);
+}
+
+// State from macroscopic fields: reference moments n^s = rho^s/m^s, u, T
+// and zero deviations.
+template <int S>
+__global__ void __launch_bounds__(256)
+    k_set_state_bf16(BfState st, int nx, int ny, int pitch, int bc_x, int bc_y, const double *__restrict__ rho_s,
+                     const double *__restrict__ ux, const double *__restrict__ uy, const double *__restrict__ T,
+                     const __grid_constant__ OutConsts<S> oc)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= nx || y >= ny) return;
+    const long long N = (long long)nx * ny, d = (long long)y * nx + x;
+    const long long cell = (long long)(y + GY) * pitch + (x + GX);
+    const Images im = cell_images(x, y, nx, ny, bc_x, bc_y);
+    for (int s = 0; s < S; ++s) {
+        store_with_images(st.mom + (long long)s * st.P, cell, x, y, pitch, im, (float)(rho_s[s * N + d] / oc.m[s]));
+        for (int i = 0; i < Q; ++i)
+            store_with_images(st.d + (long long)(s * Q + i) * st.P, cell, x, y, pitch, im, __float2bfloat16_rn(0.0f));
+    }
+    store_with_images(st.mom + (long long)S * st.P, cell, x, y, pitch, im, (float)ux[d]);
+    store_with_images(st.mom + (long long)(S + 1) * st.P, cell, x, y, pitch, im, (float)uy[d]);
+    store_with_images(st.mom + (long long)(S + 2) * st.P, cell, x, y, pitch, im, (float)T[d]);
+}
+
+// State from raw distributions (FP64 dense): reference moments are the
+// moments of f (species n^s; mixture u, T as the collision defines them,
+// in FP64), deviations f - f^eq(moments) rounded to bfloat16.
+template <int S>
+__global__ void __launch_bounds__(128)
+    k_set_f_bf16(const __grid_constant__ StepConsts<float, S> k, const __grid_constant__ OutConsts<S> oc, BfState st,
+                 const double *__restrict__ src)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= oc.nx || y >= oc.ny) return;
+    const long long N = (long long)oc.nx * oc.ny, d = (long long)y * oc.nx + x;
+    const long long cell = (long long)(y + GY) * oc.pitch + (x + GX);
+    const Images im = cell_images(x, y, oc.nx, oc.ny, oc.bc_x, oc.bc_y);
+    double n[S], w = 0, wx = 0, wy = 0, we = 0, wd = 0;
+    for (int s = 0; s < S; ++s) {
+        double sn = 0, sx = 0, sy = 0, se = 0;
+        for (int i = 0; i < Q; ++i) {
+            const double v = src[(s * Q + i) * N + d];
+            const int r = i >> 2;
+            sn += v;
+            sx += dir_x(i) * oc.vr[s][r] * v;
+            sy += dir_y(i) * oc.vr[s][r] * v;
+            se += oc.qr[s][r] * v;
+        }
+        n[s] = sn;
+        const double mt = oc.m[s] * oc.inv_tau[s];
+        w += mt * sn;
+        wx += mt * sx;
+        wy += mt * sy;
+        we += mt * se;
+        wd += oc.dpi[s] * oc.inv_tau[s] * sn;
+    }
+    const double Ux = wx / w, Uy = wy / w;
+    const double T = (we - (Ux * Ux + Uy * Uy) * w) / wd;
+    const float ux = (float)Ux, uy = (float)Uy, Tf = (float)T;
+    store_with_images(st.mom + (long long)S * st.P, cell, x, y, oc.pitch, im, ux);
+    store_with_images(st.mom + (long long)(S + 1) * st.P, cell, x, y, oc.pitch, im, uy);
+    store_with_images(st.mom + (long long)(S + 2) * st.P, cell, x, y, oc.pitch, im, Tf);
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) {
+        const float ns = (float)n[s];
+        store_with_images(st.mom + (long long)s * st.P, cell, x, y, oc.pitch, im, ns);
+        float fe[Q];
+        feq_ref<S>(k, s, ns, ux, uy, Tf, fe);
+        for (int i = 0; i < Q; ++i)
+            store_with_images(st.d + (long long)(s * Q + i) * st.P, cell, x, y, oc.pitch, im,
+                              __float2bfloat16_rn((float)(src[(s * Q + i) * N + d] - (double)fe[i])));
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(128)
+    k_get_f_bf16(const __grid_constant__ StepConsts<float, S> k, BfState st, double *__restrict__ dst)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= k.nx || y >= k.ny) return;
+    const long long N = (long long)k.nx * k.ny, d = (long long)y * k.nx + x;
+    const long long cell = (long long)(y + GY) * k.pitch + (x + GX);
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) {
+        float f[Q];
+        bf_cell_f<S>(k, st, s, cell, f);
+        for (int i = 0; i < Q; ++i) dst[(s * Q + i) * N + d] = (double)f[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+constexpr int BF_TX = 64, BF_TY = 8;
+
+template <int S>
+static int step_bf16_t(dbm_handle *h, int cur, cudaStream_t st)
+{
+    constexpr size_t smem = (size_t)(BF_TX + 4) * (BF_TY + 4) * S * Q * sizeof(float);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_bf16<S, BF_TX, BF_TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return set_cuda_error(h, e, "BF16 step kernel shared-memory attribute");
+        attr_set = true;
+    }
+    StepConsts<float, S> c;
+    fill_step_consts<float, S>(h, c);
+    dim3 block(BF_TX / 2, BF_TY);
+    dim3 grid((h->p.nx + BF_TX - 1) / BF_TX, (h->p.ny + BF_TY - 1) / BF_TY);
+    k_step_bf16<S, BF_TX, BF_TY><<<grid, block, smem, st>>>(c, bf_state(h, h->f[cur]), bf_state(h, h->f[cur ^ 1]),
+                                                            (unsigned *)h->scratch);
+    return set_cuda_error(h, cudaGetLastError(), "BF16 step kernel launch");
+}
+
+int launch_step_bf16(dbm_handle *h, int cur, cudaStream_t st)
+{
+    switch (h->p.nspecies) {
+    case 1: return step_bf16_t<1>(h, cur, st);
+    case 2: return step_bf16_t<2>(h, cur, st);
+    case 3: return step_bf16_t<3>(h, cur, st);
+    case 4: return step_bf16_t<4>(h, cur, st);
+    }
+    return DBM_ERR_INVALID;
+}
+
+static dim3 grid_of(const dbm_handle *h, dim3 b)
+{
+    return dim3((h->p.nx + b.x - 1) / b.x, (h->p.ny + b.y - 1) / b.y);
+}
+
+template <int S>
+static void set_state_bf16_t(dbm_handle *h, void *f, const double *rho_s, const double *ux, const double *uy,
+                             const double *T, cudaStream_t st)
+{
+    OutConsts<S> oc;
+    fill_out_consts<S>(h, oc);
+    dim3 b(32, 8);
+    k_set_state_bf16<S><<<grid_of(h, b), b, 0, st>>>(bf_state(h, f), h->p.nx, h->p.ny, h->lay.pitch, h->p.bc_x,
+                                                     h->p.bc_y, rho_s, ux, uy, T, oc);
+}
+
+int launch_set_state_bf16(dbm_handle *h, void *f, const double *rho_s, const double *ux, const double *uy,
+                          const double *T, cudaStream_t st)
+{
+    switch (h->p.nspecies) {
+    case 1: set_state_bf16_t<1>(h, f, rho_s, ux, uy, T, st); break;
+    case 2: set_state_bf16_t<2>(h, f, rho_s, ux, uy, T, st); break;
+    case 3: set_state_bf16_t<3>(h, f, rho_s, ux, uy, T, st); break;
+    case 4: set_state_bf16_t<4>(h, f, rho_s, ux, uy, T, st); break;
+    default: return DBM_ERR_INVALID;
+    }
+    return set_cuda_error(h, cudaGetLastError(), "BF16 set_state kernel launch");
+}
+
+template <int S>
+static void set_f_bf16_t(dbm_handle *h, void *f, const double *src, cudaStream_t st)
+{
+    StepConsts<float, S> k;
+    fill_step_consts<float, S>(h, k);
+    OutConsts<S> oc;
+    fill_out_consts<S>(h, oc);
+    dim3 b(32, 4);
+    k_set_f_bf16<S><<<grid_of(h, b), b, 0, st>>>(k, oc, bf_state(h, f), src);
+}
+
+int launch_set_f_bf16(dbm_handle *h, void *f, const double *src, cudaStream_t st)
+{
+    switch (h->p.nspecies) {
+    case 1: set_f_bf16_t<1>(h, f, src, st); break;
+    case 2: set_f_bf16_t<2>(h, f, src, st); break;
+    case 3: set_f_bf16_t<3>(h, f, src, st); break;
+    case 4: set_f_bf16_t<4>(h, f, src, st); break;
+    default: return DBM_ERR_INVALID;
+    }
+    return set_cuda_error(h, cudaGetLastError(), "BF16 set_f kernel launch");
+}
+
+template <int S>
+static void get_f_bf16_t(dbm_handle *h, const void *f, double *dst, cudaStream_t st)
+{
+    StepConsts<float, S> k;
+    fill_step_consts<float, S>(h, k);
+    dim3 b(32, 4);
+    k_get_f_bf16<S><<<grid_of(h, b), b, 0, st>>>(k, bf_state(h, (void *)f), dst);
+}
+
+int launch_get_f_bf16(dbm_handle *h, const void *f, double *dst, cudaStream_t st)
+{
+    switch (h->p.nspecies) {
+    case 1: get_f_bf16_t<1>(h, f, dst, st); break;
+    case 2: get_f_bf16_t<2>(h, f, dst, st); break;
+    case 3: get_f_bf16_t<3>(h, f, dst, st); break;
+    case 4: get_f_bf16_t<4>(h, f, dst, st); break;
+    default: return DBM_ERR_INVALID;
+    }
+    return set_cuda_error(h, cudaGetLastError(), "BF16 get_f kernel launch");
+}
+
+}  // namespace dbm

@@ -1,0 +1,121 @@
+// dbm_bf16.cuh -- the BF16-deviation storage of the D2V16 state.
+//
+// Each cell keeps float reference moments (n^s for every species, the
+// mixture u_x, u_y and T) and, per species and velocity, a bfloat16
+// deviation delta, so that
+//     f_i^s = f^eq_i(n^s, u, T) + delta_i^s,
+// with f^eq evaluated by the FP32 symmetry-block equilibrium (feq_ref).
+// The reference moments are those of the previous state, so delta is small
+// (of the order of the nonequilibrium part plus one step's change) and its
+// 8-bit mantissa costs far less than storing f itself in 16 bits.  Every
+// reconstruction of a cell (as centre or as halo of a neighbour, in the
+// step and in the output kernels) runs feq_ref on the same stored values.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "dbm_step_impl.cuh"
+
+namespace dbm {
+
+// Reference equilibrium of species s at stored (n, u, T), FP32.
+template <int S>
+__device__ __forceinline__ void feq_ref(const StepConsts<float, S> &k, int s, float n, float ux, float uy,
+                                        float T, float f[Q])
+{
+    float c[16], o[16];
+    fhat_blocks<float>(n, ux, uy, T * k.inv_m[s], k.dpi[s], c);
+    solve_blocks<float, S>(k, s, c, o);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = feq_of<float>(i, o);
+}
+
+// Pointers of one BF16-deviation state buffer.
+struct BfState {
+    __nv_bfloat16 *d;  // 16 S deviation planes
+    float *mom;        // S + 3 moment planes: n^0..n^{S-1}, u_x, u_y, T
+    long long P;       // elements per plane
+};
+
+// Output policy of the step: delta^{n+1} = f^{n+1} - f^eq(moments of f^n)
+// (the collision equilibrium the step has just built) and those moments.
+struct BfOut {
+    BfState st;
+    int nx, ny, pitch, S;
+    __device__ __forceinline__ void put(const Site &w, int p, float g0, float g1, float e0, float e1) const
+    {
+        __nv_bfloat16 *pl = st.d + (long long)p * st.P;
+        const float d0 = g0 - e0, d1 = g1 - e1;
+        if (w.two) {
+            __stcs(reinterpret_cast<__nv_bfloat162 *>(pl + w.cell), __floats2bfloat162_rn(d0, d1));
+        } else {
+            pl[w.cell] = __float2bfloat16_rn(d0);
+        }
+        if (w.images) {
+            store_images(pl, w.x0, w.y, nx, ny, pitch, w.mx0, w.my, __float2bfloat16_rn(d0));
+            if (w.two) store_images(pl, w.x0 + 1, w.y, nx, ny, pitch, w.mx1, w.my, __float2bfloat16_rn(d1));
+        }
+    }
+    __device__ __forceinline__ void put_plane(const Site &w, int k, float v0, float v1) const
+    {
+        float *pl = st.mom + (long long)k * st.P;
+        if (w.two) {
+            __stcs(reinterpret_cast<float2 *>(pl + w.cell), make_float2(v0, v1));
+        } else {
+            pl[w.cell] = v0;
+        }
+        if (w.images) {
+            store_images(pl, w.x0, w.y, nx, ny, pitch, w.mx0, w.my, v0);
+            if (w.two) store_images(pl, w.x0 + 1, w.y, nx, ny, pitch, w.mx1, w.my, v1);
+        }
+    }
+    __device__ __forceinline__ void put_n(const Site &w, int s, float n0, float n1) const
+    {
+        put_plane(w, s, n0, n1);
+    }
+    __device__ __forceinline__ void put_mix(const Site &w, float ux0, float uy0, float T0, float ux1, float uy1,
+                                            float T1) const
+    {
+        put_plane(w, S, ux0, ux1);
+        put_plane(w, S + 1, uy0, uy1);
+        put_plane(w, S + 2, T0, T1);
+    }
+};
+
+// f of species s at one cell (element offset `cell` in a plane), FP32.
+template <int S>
+__device__ __forceinline__ void bf_cell_f(const StepConsts<float, S> &k, const BfState &st, int s, long long cell,
+                                          float f[Q])
+{
+    const float n = st.mom[(long long)s * st.P + cell];
+    const float ux = st.mom[(long long)S * st.P + cell];
+    const float uy = st.mom[(long long)(S + 1) * st.P + cell];
+    const float T = st.mom[(long long)(S + 2) * st.P + cell];
+    feq_ref<S>(k, s, n, ux, uy, T, f);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] += __bfloat162float(st.d[(long long)(s * Q + i) * st.P + cell]);
+}
+
+// Source policy of the FP64 output kernels for a BF16-deviation state.
+template <int S>
+struct BfSrc {
+    StepConsts<float, S> k;
+    BfState st;
+    __device__ __forceinline__ void load16(int s, long long cell, double v[Q]) const
+    {
+        float f[Q];
+        bf_cell_f<S>(k, st, s, cell, f);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v[i] = (double)f[i];
+    }
+};
+
+inline BfState bf_state(const dbm_handle *h, void *buf)
+{
+    BfState s;
+    s.d = (__nv_bfloat16 *)buf;
+    s.mom = (float *)((char *)buf + h->lay.moments_offset);
+    s.P = h->lay.plane;
+    return s;
+}
+
+}  // namespace dbm

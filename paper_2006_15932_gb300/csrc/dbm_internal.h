@@ -133,5 +133,10 @@ struct F64Consts {
 template <int S>
 void fill_f64_consts(const dbm_handle *h, F64Consts<S> &c);
 int launch_step_f64(dbm_handle *h, int cur, cudaStream_t st);
+int launch_step_bf16(dbm_handle *h, int cur, cudaStream_t st);
+int launch_set_state_bf16(dbm_handle *h, void *f, const double *rho_s, const double *ux, const double *uy,
+                          const double *T, cudaStream_t st);
+int launch_set_f_bf16(dbm_handle *h, void *f, const double *src, cudaStream_t st);
+int launch_get_f_bf16(dbm_handle *h, const void *f, double *dst, cudaStream_t st);
 
 }  // namespace dbm

@@ -92,6 +92,7 @@ int launch_step(dbm_handle *h, int cur, cudaStream_t st)
         }
     }
     if (want == DBM_KERNEL_TMA) return DBM_ERR_INVALID;
+    if (h->p.precision == DBM_BF16DEV) return launch_step_bf16(h, cur, st);
     if (h->p.precision == DBM_FP64) return launch_step_f64(h, cur, st);
     if (h->p.precision == DBM_FP32) return launch_generic<float>(h, fin, fout, st);
     return DBM_ERR_INVALID;

@@ -232,10 +232,46 @@ __device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux,
     return T;
 }
 
+// Where the pair sits: interior coordinates, whether the second cell
+// exists, and the ghost images its values must also be written to.
+struct Site {
+    int x0, y;
+    bool two, images;
+    unsigned mx0, mx1, my;
+    long long cell;  // element offset of (x0, y) in a plane
+};
+
+// Output of the FP32 state: f^{n+1} as a pair, plus ghost images.
+template <typename real>
+struct StateOut {
+    using R2 = typename Vec2<real>::t;
+    real *f;  // plane 0 of the output buffer
+    long long P;
+    int nx, ny, pitch;
+    __device__ __forceinline__ void put(const Site &w, int p, real g0, real g1, real, real) const
+    {
+        real *pl = f + (long long)p * P;
+        if (w.two) {
+            R2 v;
+            v.x = g0;
+            v.y = g1;
+            __stcs(reinterpret_cast<R2 *>(pl + w.cell), v);  // streamed: not re-read this step
+        } else {
+            __stcs(pl + w.cell, g0);
+        }
+        if (w.images) {
+            store_images(pl, w.x0, w.y, nx, ny, pitch, w.mx0, w.my, g0);
+            if (w.two) store_images(pl, w.x0 + 1, w.y, nx, ny, pitch, w.mx1, w.my, g1);
+        }
+    }
+    __device__ __forceinline__ void put_n(const Site &, int, real, real) const {}
+    __device__ __forceinline__ void put_mix(const Site &, real, real, real, real, real, real) const {}
+};
+
 // The whole update of the cell pair (x0, y), (x0+1, y).
-template <typename real, int S, class Tile>
+template <typename real, int S, class Tile, class Out>
 __device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Tile &t, int x0, int y,
-                                          real *__restrict__ fout, unsigned *__restrict__ flag)
+                                          const Out &out, unsigned *__restrict__ flag)
 {
     using R2 = typename Vec2<real>::t;
     const bool two = x0 + 1 < c.nx;
@@ -244,6 +280,7 @@ __device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Ti
 
     // 1. species moments of both cells, by ring sums
     real n0[S], n1[S], cap0 = 0, cap1 = 0;
+    real nf0 = 0, nf1 = 0, no0 = 0, no1 = 0;  // fuel and oxidiser densities
     real w0 = 0, w1 = 0, wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0, we0 = 0, we1 = 0, wd0 = 0, wd1 = 0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -273,6 +310,8 @@ __device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Ti
         }
         n0[s] = sn0;
         n1[s] = sn1;
+        if (s == c.fuel) { nf0 = sn0; nf1 = sn1; }  // no runtime-indexed register array
+        if (s == c.oxid) { no0 = sn0; no1 = sn1; }
         const real lh = c.lam_h[s], ll = c.lam_l[s], kh = c.kap_h[s], kl = c.kap_l[s];
         w0 += lh * sn0 + ll * sn0;
         w1 += lh * sn1 + ll * sn1;
@@ -311,19 +350,25 @@ __device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Ti
     // 3. reaction: omega_ov and T' (state after a time tau^s), FP64
     double om0 = 0.0, om1 = 0.0, dT0 = 0.0, dT1 = 0.0;
     if (c.has_reaction) {
-        om0 = c.k_ov * (double)n0[c.fuel] * (double)n0[c.oxid] * exp(-c.Ea_over_R / T0d);
-        om1 = c.k_ov * (double)n1[c.fuel] * (double)n1[c.oxid] * exp(-c.Ea_over_R / T1d);
+        om0 = c.k_ov * (double)nf0 * (double)no0 * exp(-c.Ea_over_R / T0d);
+        om1 = c.k_ov * (double)nf1 * (double)no1 * exp(-c.Ea_over_R / T1d);
         dT0 = (c.Qheat - 0.5 * T0d * c.src) * om0 / (0.5 * (double)cap0);
         dT1 = (c.Qheat - 0.5 * T1d * c.src) * om1 / (0.5 * (double)cap1);
     }
 
-    const unsigned mx0 = ghost_mask(x0, c.nx, c.bc_x), mx1 = two ? ghost_mask(x0 + 1, c.nx, c.bc_x) : 0u;
-    const unsigned my = ghost_mask(y, c.ny, c.bc_y);
-    const bool images = (mx0 | mx1 | my) != 0u;
+    Site w;
+    w.x0 = x0;
+    w.y = y;
+    w.two = two;
+    w.mx0 = ghost_mask(x0, c.nx, c.bc_x);
+    w.mx1 = two ? ghost_mask(x0 + 1, c.nx, c.bc_x) : 0u;
+    w.my = ghost_mask(y, c.ny, c.bc_y);
+    w.images = (w.mx0 | w.mx1 | w.my) != 0u;
+    w.cell = cell;
+    out.put_mix(w, ux0, uy0, T0, ux1, uy1, T1);
 
 #pragma unroll 1
     for (int s = 0; s < S; ++s) {
-        real *gs = fout + (long long)(s * Q) * P + cell;
         // centres of this species, both cells
         real f0[Q], f1[Q];
 #pragma unroll
@@ -334,13 +379,14 @@ __device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Ti
         }
         // 4. merged equilibrium moments of both cells
         real cb0[16], cb1[16];
-        {
-            real ns0 = 0, ns1 = 0;
+        real ns0 = 0, ns1 = 0;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                ns0 += f0[i];
-                ns1 += f1[i];
-            }
+        for (int i = 0; i < Q; ++i) {
+            ns0 += f0[i];
+            ns1 += f1[i];
+        }
+        out.put_n(w, s, ns0, ns1);
+        {
             real nr0 = ns0, nr1 = ns1;
             real Ts0 = T0, Ts1 = T1;
             if (c.has_reaction) {
@@ -418,22 +464,10 @@ __device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Ti
                 d1 -= cy * nnd_diff_neg(m1.y, f1[i], p1.y, p2.y);
             }
             // 6. forward Euler: f + dt/tau (f^eq,tot - f) - dt v . grad f
-            const real g0 = f0[i] + dtt * (feq_of<real>(i, o0) - f0[i]) - d0;
-            const real g1 = f1[i] + dtt * (feq_of<real>(i, o1) - f1[i]) - d1;
-            real *po = gs + i * P;
-            if (two) {
-                R2 v;
-                v.x = g0;
-                v.y = g1;
-                __stcs(reinterpret_cast<R2 *>(po), v);  // streamed: not re-read this step
-            } else {
-                __stcs(po, g0);
-            }
-            if (images) {
-                real *plo = fout + (long long)p * P;
-                store_images(plo, x0, y, c.nx, c.ny, c.pitch, mx0, my, g0);
-                if (two) store_images(plo, x0 + 1, y, c.nx, c.ny, c.pitch, mx1, my, g1);
-            }
+            const real e0 = feq_of<real>(i, o0), e1 = feq_of<real>(i, o1);
+            const real g0 = f0[i] + dtt * (e0 - f0[i]) - d0;
+            const real g1 = f1[i] + dtt * (e1 - f1[i]) - d1;
+            out.put(w, p, g0, g1, e0, e1);
         }
     }
     if (bad) raise_flag(flag, bad);
@@ -452,7 +486,8 @@ __global__ void __launch_bounds__(256, 2)
     t.base = fin + (long long)(y + GY) * c.pitch + (x0 + GX);
     t.P = c.plane;
     t.py = c.pitch;
-    step_pair<real, S>(c, t, x0, y, fout, flag);
+    StateOut<real> o{fout, c.plane, c.nx, c.ny, c.pitch};
+    step_pair<real, S>(c, t, x0, y, o, flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -529,7 +564,8 @@ __global__ void __launch_bounds__((TX / 2) * TY, 2)
     t.base = tile + (ty + 2) * BX + (2 * tx + 4);
     t.P = BY * BX;
     t.py = BX;
-    step_pair<real, S>(c, t, x0, y, fout, flag);
+    StateOut<real> o{fout, c.plane, c.nx, c.ny, c.pitch};
+    step_pair<real, S>(c, t, x0, y, o, flag);
 }
 
 template <typename real, int S>

@@ -177,3 +177,18 @@ def _moment_matrix_from_velocities(sp):
         M[:, i] = [1.0, x, y, q, x * x, x * y, y * y, q * x, q * y, x * x * x, x * x * y, x * y * y,
                    y * y * y, q * x * x, q * x * y, q * y * y]
     return M
+
+
+def test_bf16dev_scope(D):
+    """BF16-deviation storage: up to 4 species, no reaction, no force."""
+    pb = W.random_smooth(8, 8, 2)
+    h = D.dbm_init(D.params_from_problem(pb, "bf16dev"))
+    lay = D.dbm_get_layout(h)
+    assert lay.elem_bytes == 2 and lay.moments_offset % 256 == 0
+    assert lay.bytes == lay.moments_offset + (2 + 3) * lay.plane * 4
+    D.dbm_destroy(h)
+    for bad in (W.random_smooth(8, 8, 3, reactive=True), W.random_smooth(8, 8, 2, force=True),
+                W.random_smooth(8, 8, 5)):
+        with pytest.raises(D.DbmError) as e:
+            D.dbm_init(D.params_from_problem(bad, "bf16dev"))
+        assert "BF16DEV" in str(e.value)
