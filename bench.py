@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="kh4096", choices=["kh4096", "reactive", "sod"])
+    ap.add_argument("--workload", default="kh4096", choices=["kh4096", "reactive", "sod", "batched"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and e2e side legs")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -274,14 +274,43 @@ def main():
         dist.barrier()
     D.load()
 
-    pb = make_workload(args.workload, args.grid)
-    cfg = workload_config(pb, args.workload, args.precision)
     stream = torch.cuda.Stream(device=dev)
-    solver = D.Solver(pb, args.precision, device=dev, stream=stream)
-    with torch.cuda.stream(stream):
+    if args.workload == "batched":
+        from paper_2006_15932_gb300 import workloads as W
+
+        pbs = W.batched_instances()
+        pb = pbs[0]
+        cfg = {"workload": "batched_shock_and_reactive_instances", "instances": len(pbs),
+               "grids": "square, sides uniform in [64, 512] (seeded)", "species": 2, "velocities": 16,
+               "precision": args.precision, "cells": sum(q.nx * q.ny for q in pbs),
+               "l2_policy": "inputs larger than L2",
+               "launch": "one persistent launch per step, pairs of steps replayed from a CUDA graph"}
+        solvers = [D.Solver(q, args.precision, device=dev, stream=stream) for q in pbs]
+        for s_ in solvers:
+            s_.set_state()
+        batch = D.Batch(solvers, stream=stream, tune=True)
+        cfg["tile"] = list(batch.info()["tile"])
+        units = sum(q.nx * q.ny * q.ns for q in pbs)
+        per_call = 2  # one graph replay = two steps
+
+        def advance(n):
+            batch.step(n)
+
+        solver = solvers[0]
+    else:
+        pb = make_workload(args.workload, args.grid)
+        cfg = workload_config(pb, args.workload, args.precision)
+        solver = D.Solver(pb, args.precision, device=dev, stream=stream)
         solver.set_state()
+        units = pb.nx * pb.ny * pb.ns
+        per_call = 1
+
+        def advance(n):
+            solver.step(n)
+
+    with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
-            solver.step(1)
+            advance(per_call)
     torch.cuda.synchronize(dev)
 
     uuid = None
@@ -290,8 +319,9 @@ def main():
     except Exception:
         pass
     clocks = ClockSampler(uuid)
-    K = args.steps
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    K = max(per_call, args.steps // per_call * per_call)
+    calls = K // per_call
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(calls + 1)]
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -299,41 +329,43 @@ def main():
     time.sleep(0.25)  # let the sampler start
     with torch.cuda.stream(stream):
         ev[0].record(stream)
-        for k in range(K):
-            solver.step(1)
+        for k in range(calls):
+            advance(per_call)
             ev[k + 1].record(stream)
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     if dist is not None:
         dist.barrier()
-    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
-    ms_total = ev[0].elapsed_time(ev[K])
-    rc, bits = solver.status()
-    if rc != 0:
-        raise SystemExit(f"health flag raised during the benchmark: rc={rc} bits={bits}")
+    per_launch = [ev[k].elapsed_time(ev[k + 1]) / per_call for k in range(calls)]
+    ms_total = ev[0].elapsed_time(ev[calls])
+    for s_ in (solvers if args.workload == "batched" else [solver]):
+        rc, bits = s_.status()
+        if rc != 0:
+            raise SystemExit(f"health flag raised during the benchmark: rc={rc} bits={bits}")
     ms = torch.tensor([ms_total], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(ms, op=dist.ReduceOp.MAX)
     ms_max = float(ms.item())
-    updates_per_rank = pb.nx * pb.ny * pb.ns * K
+    updates_per_rank = units * K
     value = updates_per_rank * world / (ms_max * 1e-3)
 
     peak, peak_kind = measured_peaks()
     bpu = bytes_per_update(args.precision, pb.ns)
     avg_launch_ms = statistics.mean(per_launch)
-    bytes_per_launch = pb.nx * pb.ny * pb.ns * bpu
+    bytes_per_launch = units * bpu
     achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload, args.precision)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": step_kernel_name(pb, args.precision),
+                "kernel": step_kernel_name(pb, args.precision) if args.workload != "batched"
+                else f"k_step_batch<{pb.ns},{cfg['tile'][0]},{cfg['tile'][1]}>",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "median_launch_ms": statistics.median(per_launch)}
 
     extras = {}
     e2e = None
-    if not args.no_extras:
+    if not args.no_extras and args.workload != "batched":
         e2e = measure_e2e(D, pb, args.precision, dev, stream)
         if args.precision == "fp32" and rank == 0:
             extras["fp64"] = measure_fp64(D, pb, dev, stream)
@@ -346,7 +378,12 @@ def main():
     line.update(extras)
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(pb, args.precision, args.cpu_seconds)
-    solver.close()
+    if args.workload == "batched":
+        batch.close()
+        for s_ in solvers:
+            s_.close()
+    else:
+        solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

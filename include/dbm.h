@@ -202,6 +202,45 @@ int dbm_nonequilibrium(dbm_handle *h, double *out, void *stream);
  * Uses the bound scratch buffer.  Async on stream. */
 int dbm_conservation(dbm_handle *h, double *out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent problems stepped together.
+ *
+ * A batch groups bound FP32 handles with the same species count S <= 3
+ * (grids, boundaries, species constants, reaction and time step may all
+ * differ).  Each dbm_batch_step advances every instance: one persistent
+ * kernel launch per time step walks the tiles of all instances, each tile
+ * staged by TMA through its instance's own descriptor; pairs of steps are
+ * replayed from captured CUDA graphs when `stream` is a created stream.
+ * The caller owns the device table (dbm_batch_table_bytes, 128-byte
+ * aligned).  While a batch exists, step its handles through it; a handle
+ * reset with dbm_set_state / dbm_set_f is picked up on the next batch step.
+ * ------------------------------------------------------------------------ */
+typedef struct dbm_batch dbm_batch;
+
+/* Bytes of the device table for these n handles. */
+int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes);
+
+/* Build a batch over n handles; writes the table (async on stream, then
+ * synchronises it).  DBM_ERR_INVALID if a handle is unbound, not FP32, has
+ * S > 3 or a different S than the others, or the table is too small. */
+int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t table_bytes, void *stream,
+                     dbm_batch **out);
+
+/* Choose the tile shape (64x8, 32x8 or 32x16 cells) that steps this batch
+ * fastest: each shape is timed on `reps` trial launches that read the
+ * current states and write only the buffers the next step overwrites, so
+ * no state advances.  Synchronises the stream. */
+int dbm_batch_tune(dbm_batch *b, void *stream, int reps);
+
+/* Advance every instance of the batch by nsteps >= 0 (async on stream). */
+int dbm_batch_step(dbm_batch *b, int nsteps, void *stream);
+
+/* Current tile shape, number of tiles per step and persistent CTAs. */
+int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int *ctas);
+
+const char *dbm_batch_last_error(const dbm_batch *b);
+void dbm_batch_destroy(dbm_batch *b);
+
 /* Capacity, in doubles, of the library's own device array that holds the
  * reduction partials of dbm_conservation_noalloc (32 KB on every GPU that
  * loads the library, kept until the process exits). */

@@ -3,8 +3,8 @@
 //
 // One CTA steps a TX x TY tile.  Phase A rebuilds f (FP32) of the tile and
 // its radius-2 halo in shared memory from the stored moments and bfloat16
-// deviations; phase B runs the same per-pair FP32 arithmetic as the FP32
-// kernels (step_pair) on that tile and stores delta^{n+1} and the
+// deviations; phase B runs the same per-cell FP32 arithmetic as the FP32
+// kernels (step_cell) on that tile and stores delta^{n+1} and the
 // reference moments.  Reactions and forces are not supported in this
 // storage (their equilibrium is not the one of the stored moments); init
 // rejects them.
@@ -13,47 +13,43 @@
 namespace dbm {
 
 template <int S, int TX, int TY>
-__global__ void __launch_bounds__((TX / 2) * TY, 2)
+__global__ void __launch_bounds__(TX *TY, 2)
     k_step_bf16(const __grid_constant__ StepConsts<float, S> c, BfState in, BfState out,
                 unsigned *__restrict__ flag)
 {
-    constexpr int BX = TX + 4, BY = TY + 4, NP = S * Q, NPAIR = BX / 2;
+    constexpr int BX = TX + 4, BY = TY + 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *tile = reinterpret_cast<float *>(smem_raw);  // [NP][BY][BX], column 0 = x0 - 2
+    float *tile = reinterpret_cast<float *>(smem_raw);  // [16 S][BY][BX], column 0 = x0 - 2
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int nthr = (TX / 2) * TY, tid = ty * (TX / 2) + tx;
+    const int nthr = TX * TY, tid = ty * TX + tx;
     const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
 
-    // phase A: rebuild f for the tile and its halo, pairs of cells
-    for (int k = tid; k < NPAIR * BY; k += nthr) {
-        const int rr = k / NPAIR, pc = k % NPAIR;
-        const int x = bx0 - 2 + 2 * pc, y = by0 - 2 + rr;
-        const bool ok0 = x <= c.nx + 1 && y <= c.ny + 1;  // inside the ghost band
-        const bool ok1 = x + 1 <= c.nx + 1 && ok0;
+    // phase A: rebuild f for the tile and its halo
+    for (int k = tid; k < BX * BY; k += nthr) {
+        const int rr = k / BX, cc = k % BX;
+        const int x = bx0 - 2 + cc, y = by0 - 2 + rr;
+        const bool ok = x <= c.nx + 1 && y <= c.ny + 1;  // inside the ghost band
         const long long cell = (long long)(y + GY) * c.pitch + (x + GX);
-        float *dst = tile + rr * BX + 2 * pc;
+        float *dst = tile + rr * BX + cc;
 #pragma unroll 1
         for (int s = 0; s < S; ++s) {
-            float f0[Q], f1[Q];
-            if (ok0) bf_cell_f<S>(c, in, s, cell, f0);
-            if (ok1) bf_cell_f<S>(c, in, s, cell + 1, f1);
+            float f[Q];
+            if (ok) bf_cell_f<S>(c, in, s, cell, f);
 #pragma unroll
-            for (int i = 0; i < Q; ++i)
-                *reinterpret_cast<float2 *>(dst + (s * Q + i) * (BY * BX)) =
-                    make_float2(ok0 ? f0[i] : 0.0f, ok1 ? f1[i] : 0.0f);
+            for (int i = 0; i < Q; ++i) dst[(s * Q + i) * (BY * BX)] = ok ? f[i] : 0.0f;
         }
     }
     __syncthreads();
 
     // phase B: the step from shared memory
-    const int x0 = bx0 + 2 * tx, y = by0 + ty;
-    if (x0 >= c.nx || y >= c.ny) return;
-    SmemTile<float> t;
-    t.base = tile + (ty + 2) * BX + (2 * tx + 2);
+    const int x = bx0 + tx, y = by0 + ty;
+    if (x >= c.nx || y >= c.ny) return;
+    SmemTile t;
+    t.base = tile + (ty + 2) * BX + (tx + 2);
     t.P = BY * BX;
     t.py = BX;
     BfOut o{out, c.nx, c.ny, c.pitch, S};
-    step_pair<float, S>(c, t, x0, y, o, flag);
+    step_cell<S>(c, t, x, y, o, flag);
 }
 
 // State from macroscopic fields: reference moments n^s = rho^s/m^s, u, T
@@ -167,7 +163,7 @@ static int step_bf16_t(dbm_handle *h, int cur, cudaStream_t st)
     }
     StepConsts<float, S> c;
     fill_step_consts<float, S>(h, c);
-    dim3 block(BF_TX / 2, BF_TY);
+    dim3 block(BF_TX, BF_TY);
     dim3 grid((h->p.nx + BF_TX - 1) / BF_TX, (h->p.ny + BF_TY - 1) / BF_TY);
     k_step_bf16<S, BF_TX, BF_TY><<<grid, block, smem, st>>>(c, bf_state(h, h->f[cur]), bf_state(h, h->f[cur ^ 1]),
                                                             (unsigned *)h->scratch);

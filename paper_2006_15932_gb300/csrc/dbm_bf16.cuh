@@ -24,7 +24,7 @@ __device__ __forceinline__ void feq_ref(const StepConsts<float, S> &k, int s, fl
 {
     float c[16], o[16];
     fhat_blocks<float>(n, ux, uy, T * k.inv_m[s], k.dpi[s], c);
-    solve_blocks<float, S>(k, s, c, o);
+    solve_blocks<float>(k, s, c, o);
 #pragma unroll
     for (int i = 0; i < Q; ++i) f[i] = feq_of<float>(i, o);
 }
@@ -37,47 +37,41 @@ struct BfState {
 };
 
 // Output policy of the step: delta^{n+1} = f^{n+1} - f^eq(moments of f^n)
-// (the collision equilibrium the step has just built) and those moments.
+// (the collision equilibrium the step has just built) and those moments;
+// ghost images after a species / the mixture is complete (the thread
+// re-reads its own stores).
 struct BfOut {
     BfState st;
     int nx, ny, pitch, S;
-    __device__ __forceinline__ void put(const Site &w, int p, float g0, float g1, float e0, float e1) const
+    __device__ __forceinline__ void put(const Site &w, int p, float g, float e) const
     {
-        __nv_bfloat16 *pl = st.d + (long long)p * st.P;
-        const float d0 = g0 - e0, d1 = g1 - e1;
-        if (w.two) {
-            __stcs(reinterpret_cast<__nv_bfloat162 *>(pl + w.cell), __floats2bfloat162_rn(d0, d1));
-        } else {
-            pl[w.cell] = __float2bfloat16_rn(d0);
-        }
-        if (w.images) {
-            store_images(pl, w.x0, w.y, nx, ny, pitch, w.mx0, w.my, __float2bfloat16_rn(d0));
-            if (w.two) store_images(pl, w.x0 + 1, w.y, nx, ny, pitch, w.mx1, w.my, __float2bfloat16_rn(d1));
-        }
+        __stcs(st.d + (long long)p * st.P + w.cell, __float2bfloat16_rn(g - e));
     }
-    __device__ __forceinline__ void put_plane(const Site &w, int k, float v0, float v1) const
+    __device__ __forceinline__ void put_n(const Site &w, int s, float n) const
     {
-        float *pl = st.mom + (long long)k * st.P;
-        if (w.two) {
-            __stcs(reinterpret_cast<float2 *>(pl + w.cell), make_float2(v0, v1));
-        } else {
-            pl[w.cell] = v0;
-        }
-        if (w.images) {
-            store_images(pl, w.x0, w.y, nx, ny, pitch, w.mx0, w.my, v0);
-            if (w.two) store_images(pl, w.x0 + 1, w.y, nx, ny, pitch, w.mx1, w.my, v1);
-        }
+        __stcs(st.mom + (long long)s * st.P + w.cell, n);
     }
-    __device__ __forceinline__ void put_n(const Site &w, int s, float n0, float n1) const
+    __device__ __forceinline__ void put_mix(const Site &w, float ux, float uy, float T) const
     {
-        put_plane(w, s, n0, n1);
+        __stcs(st.mom + (long long)S * st.P + w.cell, ux);
+        __stcs(st.mom + (long long)(S + 1) * st.P + w.cell, uy);
+        __stcs(st.mom + (long long)(S + 2) * st.P + w.cell, T);
     }
-    __device__ __forceinline__ void put_mix(const Site &w, float ux0, float uy0, float T0, float ux1, float uy1,
-                                            float T1) const
+    __device__ __forceinline__ void images(const Site &w, int s) const
     {
-        put_plane(w, S, ux0, ux1);
-        put_plane(w, S + 1, uy0, uy1);
-        put_plane(w, S + 2, T0, T1);
+        for (int i = 0; i < Q; ++i) {
+            __nv_bfloat16 *pl = st.d + (long long)(s * Q + i) * st.P;
+            store_images(pl, w.x, w.y, nx, ny, pitch, w.mx, w.my, pl[w.cell]);
+        }
+        float *pn = st.mom + (long long)s * st.P;
+        store_images(pn, w.x, w.y, nx, ny, pitch, w.mx, w.my, pn[w.cell]);
+    }
+    __device__ __forceinline__ void images_mix(const Site &w) const
+    {
+        for (int k = S; k < S + 3; ++k) {
+            float *pl = st.mom + (long long)k * st.P;
+            store_images(pl, w.x, w.y, nx, ny, pitch, w.mx, w.my, pl[w.cell]);
+        }
     }
 };
 

@@ -8,13 +8,14 @@
 
 namespace dbm {
 
-template <typename real, int S>
+template <int S>
 int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st);
-template <typename real, int S, int TX, int TY>
+template <int S, int TX, int TY>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, void *fout, cudaStream_t st);
 
-// Tile shapes of the TMA-staged kernel (FP32): 64 x 8 cells for one or two
-// species (110.6 KB of shared memory for two), 32 x 8 for three.
+// Tile shapes of the TMA-staged kernel (FP32, one cell per thread): 64 x 8
+// cells for one or two species (110.6 KB of shared memory for two, two
+// CTAs of 512 threads per SM), 32 x 8 for three.
 bool tma_supported(const dbm_params &p) { return p.precision == DBM_FP32 && p.nspecies <= 3; }
 
 static int tma_box(const dbm_params &p, unsigned box[3])
@@ -62,18 +63,17 @@ int make_tensor_maps(dbm_handle *h)
     return DBM_OK;
 }
 
-template <typename real>
 static int launch_generic(dbm_handle *h, const void *fin, void *fout, cudaStream_t st)
 {
     switch (h->p.nspecies) {
-    case 1: return launch_step_t<real, 1>(h, fin, fout, st);
-    case 2: return launch_step_t<real, 2>(h, fin, fout, st);
-    case 3: return launch_step_t<real, 3>(h, fin, fout, st);
-    case 4: return launch_step_t<real, 4>(h, fin, fout, st);
-    case 5: return launch_step_t<real, 5>(h, fin, fout, st);
-    case 6: return launch_step_t<real, 6>(h, fin, fout, st);
-    case 7: return launch_step_t<real, 7>(h, fin, fout, st);
-    case 8: return launch_step_t<real, 8>(h, fin, fout, st);
+    case 1: return launch_step_t<1>(h, fin, fout, st);
+    case 2: return launch_step_t<2>(h, fin, fout, st);
+    case 3: return launch_step_t<3>(h, fin, fout, st);
+    case 4: return launch_step_t<4>(h, fin, fout, st);
+    case 5: return launch_step_t<5>(h, fin, fout, st);
+    case 6: return launch_step_t<6>(h, fin, fout, st);
+    case 7: return launch_step_t<7>(h, fin, fout, st);
+    case 8: return launch_step_t<8>(h, fin, fout, st);
     }
     return DBM_ERR_INVALID;
 }
@@ -86,15 +86,15 @@ int launch_step(dbm_handle *h, int cur, cudaStream_t st)
     if (h->tma_ok && want != DBM_KERNEL_GENERIC) {
         const CUtensorMap *tm = &h->tmap[cur];
         switch (h->p.nspecies) {
-        case 1: return launch_step_tma_t<float, 1, 64, 8>(h, tm, fout, st);
-        case 2: return launch_step_tma_t<float, 2, 64, 8>(h, tm, fout, st);
-        case 3: return launch_step_tma_t<float, 3, 32, 8>(h, tm, fout, st);
+        case 1: return launch_step_tma_t<1, 64, 8>(h, tm, fout, st);
+        case 2: return launch_step_tma_t<2, 64, 8>(h, tm, fout, st);
+        case 3: return launch_step_tma_t<3, 32, 8>(h, tm, fout, st);
         }
     }
     if (want == DBM_KERNEL_TMA) return DBM_ERR_INVALID;
     if (h->p.precision == DBM_BF16DEV) return launch_step_bf16(h, cur, st);
     if (h->p.precision == DBM_FP64) return launch_step_f64(h, cur, st);
-    if (h->p.precision == DBM_FP32) return launch_generic<float>(h, fin, fout, st);
+    if (h->p.precision == DBM_FP32) return launch_generic(h, fin, fout, st);
     return DBM_ERR_INVALID;
 }
 

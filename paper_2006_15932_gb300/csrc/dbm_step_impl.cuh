@@ -1,8 +1,7 @@
-// dbm_step_impl.cuh -- the fused per-timestep update of the D2V16 DBM.
+// dbm_step_impl.cuh -- the fused per-timestep update of the D2V16 DBM (FP32).
 //
-// One thread owns two horizontally adjacent cells (x0, y), (x0+1, y) and
-// computes (section "Discrete Boltzmann model" and section "Numerical
-// simulation" of arXiv 2006.15932):
+// One thread owns one cell and computes (section "Discrete Boltzmann model"
+// and section "Numerical simulation" of arXiv 2006.15932):
 //   1. species moments n^s, n^s u^s, E^s = sum f (v.v + eta^2) by ring sums;
 //   2. mixture u, T for which the collision conserves momentum and energy
 //      (the energy-minus-kinetic subtraction of T in FP64);
@@ -12,12 +11,13 @@
 //      Omega + R + G = (f^eq,tot - f) / tau (Eqs. CollisionTerm,
 //      ReactionTerm, ForceTerm: f^eq is linear in f-hat).  M^-1 is applied
 //      in the symmetry-adapted basis of D2V16 (see below);
-//   5. the NND flux differences of v_i . grad f along x (faces shared by
-//      the two cells) and y;
-//   6. the forward-Euler update, stored as a pair to the other buffer with
-//      the ghost images the boundary conditions ask for.
+//   5. the NND flux differences of v_i . grad f along x and y;
+//   6. the forward-Euler update, stored to the other buffer, then the ghost
+//      images the boundary conditions ask for (edge cells only).
 // The inputs come from a Tile policy: straight from global memory (k_step)
-// or from a shared-memory tile that one TMA bulk copy filled (k_step_tma).
+// or from a shared-memory tile that one TMA bulk copy filled (k_step_tma);
+// the outputs go through an Out policy (FP32 state, or the BF16-deviation
+// state of dbm_bf16.cuh).
 //
 // Symmetry-adapted equilibrium.  Each ring of four velocities splits into
 // a ring mean A, a vector part (E_x, E_y on the axis rings, G_x, G_y on the
@@ -49,40 +49,19 @@
 
 namespace dbm {
 
-template <typename real>
-struct Vec2;
-template <>
-struct Vec2<float> {
-    using t = float2;
-};
-template <>
-struct Vec2<double> {
-    using t = double2;
-};
-
-// Pairs of cells straight from global memory (read-only path).
-template <typename real>
+// Stencil values of one cell straight from global memory (read-only path).
 struct GlobalTile {
-    using R2 = typename Vec2<real>::t;
-    const real *base;  // plane 0, row y + GY, column x0 + GX
-    long long P;       // plane stride
-    long long py;      // row stride
-    __device__ __forceinline__ R2 ld(int p, int dx, int dy) const
-    {
-        return __ldg(reinterpret_cast<const R2 *>(base + p * P + dy * py + dx));
-    }
+    const float *base;  // plane 0, row y + GY, column x + GX
+    long long P;        // plane stride
+    long long py;       // row stride
+    __device__ __forceinline__ float ld(int p, int dx, int dy) const { return __ldg(base + p * P + dy * py + dx); }
 };
 
-// Pairs of cells from a shared-memory tile [plane][row][column].
-template <typename real>
+// Stencil values of one cell from a shared-memory tile [plane][row][column].
 struct SmemTile {
-    using R2 = typename Vec2<real>::t;
-    const real *base;  // plane 0, this thread's row and first column
+    const float *base;  // plane 0, this thread's row and column
     int P, py;
-    __device__ __forceinline__ R2 ld(int p, int dx, int dy) const
-    {
-        return *reinterpret_cast<const R2 *>(base + p * P + dy * py + dx);
-    }
+    __device__ __forceinline__ float ld(int p, int dx, int dy) const { return base[p * P + dy * py + dx]; }
 };
 
 // The 16 combinations of f-hat that feed the symmetry blocks, for one cell:
@@ -115,9 +94,8 @@ __device__ __forceinline__ void fhat_blocks(real n, real ux, real uy, real th, r
 
 // Solve the symmetry blocks (out: ring means A[4], B[2], H[2], X[4], Y[4])
 // and project the result onto exact mass, energy and momentum.
-template <typename real, int S>
-__device__ __forceinline__ void solve_blocks(const StepConsts<real, S> &k, int s, const real c[16],
-                                             real o[16])
+template <typename real, class K>
+__device__ __forceinline__ void solve_blocks(const K &k, int s, const real c[16], real o[16])
 {
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -165,31 +143,6 @@ __device__ __forceinline__ real feq_of(int i, const real o[16])
                                                                           : (A - H) - (Y - X);
 }
 
-// NND flux differences along x for the two cells x0, x0+1 from
-// f[x0-2 .. x0+3] = l0, l1, c0, c1, r0, r1: (H_{j+1/2} - H_{j-1/2}) / c for
-// both cells, with H/c = f_j + mm(.,.)/2 (c > 0) or f_{j+1} - mm(.,.)/2
-// (c < 0).  The face between the two cells is computed once.
-template <typename real>
-__device__ __forceinline__ void nnd_x_pair(int sgn, real l0, real l1, real c0, real c1, real r0, real r1,
-                                           real &o0, real &o1)
-{
-    if (sgn > 0) {
-        const real dm32 = l1 - l0, dm12 = c0 - l1, dp12 = c1 - c0, dp32 = r0 - c1;
-        const real hm = l1 + real(0.5) * minmod(dm32, dm12);  // face x0 - 1/2
-        const real h0 = c0 + real(0.5) * minmod(dm12, dp12);  // face x0 + 1/2
-        const real hp = c1 + real(0.5) * minmod(dp12, dp32);  // face x0 + 3/2
-        o0 = h0 - hm;
-        o1 = hp - h0;
-    } else {
-        const real dm12 = c0 - l1, dp12 = c1 - c0, dp32 = r0 - c1, dp52 = r1 - r0;
-        const real hm = c0 - real(0.5) * minmod(dm12, dp12);  // face x0 - 1/2
-        const real h0 = c1 - real(0.5) * minmod(dp12, dp32);  // face x0 + 1/2
-        const real hp = r0 - real(0.5) * minmod(dp32, dp52);  // face x0 + 3/2
-        o0 = h0 - hm;
-        o1 = hp - h0;
-    }
-}
-
 // Ghost-image bitmask of interior index k on an axis of n cells: bit j set
 // when ghost index {-2, -1, n, n+1}[j] takes its value from cell k.
 __device__ __forceinline__ unsigned ghost_mask(int k, int n, int bc)
@@ -209,9 +162,9 @@ __device__ __forceinline__ unsigned ghost_mask(int k, int n, int bc)
 
 __device__ __forceinline__ int ghost_index(int j, int n) { return j < 2 ? j - 2 : n + (j - 2); }
 
-template <typename real>
-__device__ __forceinline__ void store_images(real *pl, int x, int y, int nx, int ny, int pitch,
-                                             unsigned mx, unsigned my, real v)
+template <typename T>
+__device__ __forceinline__ void store_images(T *pl, int x, int y, int nx, int ny, int pitch, unsigned mx,
+                                             unsigned my, T v)
 {
     for (int j = 0; j < 4; ++j) {
         if (mx & (1u << j)) pl[(long long)(y + GY) * pitch + (ghost_index(j, nx) + GX)] = v;
@@ -232,262 +185,190 @@ __device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux,
     return T;
 }
 
-// Where the pair sits: interior coordinates, whether the second cell
-// exists, and the ghost images its values must also be written to.
+// Where the cell sits and which ghost images its values must also reach.
 struct Site {
-    int x0, y;
-    bool two, images;
-    unsigned mx0, mx1, my;
-    long long cell;  // element offset of (x0, y) in a plane
+    int x, y;
+    unsigned mx, my;
+    long long cell;  // element offset of (x, y) in a plane
 };
 
-// Output of the FP32 state: f^{n+1} as a pair, plus ghost images.
-template <typename real>
+// Output of the FP32 state: f^{n+1}; ghost images of a species after all
+// 16 of its values are stored (the thread re-reads its own stores).
 struct StateOut {
-    using R2 = typename Vec2<real>::t;
-    real *f;  // plane 0 of the output buffer
+    float *f;  // plane 0 of the output buffer
     long long P;
     int nx, ny, pitch;
-    __device__ __forceinline__ void put(const Site &w, int p, real g0, real g1, real, real) const
+    __device__ __forceinline__ void put(const Site &w, int p, float g, float) const
     {
-        real *pl = f + (long long)p * P;
-        if (w.two) {
-            R2 v;
-            v.x = g0;
-            v.y = g1;
-            __stcs(reinterpret_cast<R2 *>(pl + w.cell), v);  // streamed: not re-read this step
-        } else {
-            __stcs(pl + w.cell, g0);
-        }
-        if (w.images) {
-            store_images(pl, w.x0, w.y, nx, ny, pitch, w.mx0, w.my, g0);
-            if (w.two) store_images(pl, w.x0 + 1, w.y, nx, ny, pitch, w.mx1, w.my, g1);
+        __stcs(f + (long long)p * P + w.cell, g);  // streamed: not re-read this step
+    }
+    __device__ __forceinline__ void put_n(const Site &, int, float) const {}
+    __device__ __forceinline__ void put_mix(const Site &, float, float, float) const {}
+    __device__ __forceinline__ void images(const Site &w, int s) const
+    {
+        for (int i = 0; i < Q; ++i) {
+            float *pl = f + (long long)(s * Q + i) * P;
+            store_images(pl, w.x, w.y, nx, ny, pitch, w.mx, w.my, pl[w.cell]);
         }
     }
-    __device__ __forceinline__ void put_n(const Site &, int, real, real) const {}
-    __device__ __forceinline__ void put_mix(const Site &, real, real, real, real, real, real) const {}
+    __device__ __forceinline__ void images_mix(const Site &) const {}
 };
 
-// The whole update of the cell pair (x0, y), (x0+1, y).
-template <typename real, int S, class Tile, class Out>
-__device__ __forceinline__ void step_pair(const StepConsts<real, S> &c, const Tile &t, int x0, int y,
-                                          const Out &out, unsigned *__restrict__ flag)
+// The whole update of cell (x, y).
+template <int S, class K, class Tile, class Out>
+__device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int y, const Out &out,
+                                          unsigned *__restrict__ flag)
 {
-    using R2 = typename Vec2<real>::t;
-    const bool two = x0 + 1 < c.nx;
-    const long long P = c.plane;
-    const long long cell = (long long)(y + GY) * c.pitch + (x0 + GX);
-
-    // 1. species moments of both cells, by ring sums
-    real n0[S], n1[S], cap0 = 0, cap1 = 0;
-    real nf0 = 0, nf1 = 0, no0 = 0, no1 = 0;  // fuel and oxidiser densities
-    real w0 = 0, w1 = 0, wx0 = 0, wx1 = 0, wy0 = 0, wy1 = 0, we0 = 0, we1 = 0, wd0 = 0, wd1 = 0;
+    // 1. species moments, by ring sums
+    float n[S], cap = 0, nf = 0, no = 0;
+    float w = 0, wx = 0, wy = 0, we = 0, wd = 0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        real sn0 = 0, sn1 = 0, sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0, se0 = 0, se1 = 0;
+        float sn = 0, sx = 0, sy = 0, se = 0;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            real rs0 = 0, rs1 = 0, rx0 = 0, rx1 = 0, ry0 = 0, ry1 = 0;
+            float rs = 0, rx = 0, ry = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int i = 4 * r + k;
-                const R2 f = t.ld(s * Q + i, 0, 0);
-                rs0 += f.x;
-                rs1 += f.y;
-                if (dir_x(i) > 0) { rx0 += f.x; rx1 += f.y; }
-                if (dir_x(i) < 0) { rx0 -= f.x; rx1 -= f.y; }
-                if (dir_y(i) > 0) { ry0 += f.x; ry1 += f.y; }
-                if (dir_y(i) < 0) { ry0 -= f.x; ry1 -= f.y; }
+                const float f = t.ld(s * Q + i, 0, 0);
+                rs += f;
+                if (dir_x(i) > 0) rx += f;
+                if (dir_x(i) < 0) rx -= f;
+                if (dir_y(i) > 0) ry += f;
+                if (dir_y(i) < 0) ry -= f;
             }
-            sn0 += rs0;
-            sn1 += rs1;
-            sx0 += c.vr[s][r] * rx0;
-            sx1 += c.vr[s][r] * rx1;
-            sy0 += c.vr[s][r] * ry0;
-            sy1 += c.vr[s][r] * ry1;
-            se0 += c.qr[s][r] * rs0;
-            se1 += c.qr[s][r] * rs1;
+            sn += rs;
+            sx += c.vr[s][r] * rx;
+            sy += c.vr[s][r] * ry;
+            se += c.qr[s][r] * rs;
         }
-        n0[s] = sn0;
-        n1[s] = sn1;
-        if (s == c.fuel) { nf0 = sn0; nf1 = sn1; }  // no runtime-indexed register array
-        if (s == c.oxid) { no0 = sn0; no1 = sn1; }
-        const real lh = c.lam_h[s], ll = c.lam_l[s], kh = c.kap_h[s], kl = c.kap_l[s];
-        w0 += lh * sn0 + ll * sn0;
-        w1 += lh * sn1 + ll * sn1;
-        wx0 += lh * sx0 + ll * sx0;
-        wx1 += lh * sx1 + ll * sx1;
-        wy0 += lh * sy0 + ll * sy0;
-        wy1 += lh * sy1 + ll * sy1;
-        we0 += lh * se0 + ll * se0;
-        we1 += lh * se1 + ll * se1;
-        wd0 += kh * sn0 + kl * sn0;
-        wd1 += kh * sn1 + kl * sn1;
-        cap0 += c.dpi[s] * sn0;
-        cap1 += c.dpi[s] * sn1;
+        n[s] = sn;
+        if (s == c.fuel) nf = sn;  // selects, no runtime-indexed register array
+        if (s == c.oxid) no = sn;
+        const float lh = c.lam_h[s], ll = c.lam_l[s], kh = c.kap_h[s], kl = c.kap_l[s];
+        w += lh * sn + ll * sn;
+        wx += lh * sx + ll * sx;
+        wy += lh * sy + ll * sy;
+        we += lh * se + ll * se;
+        wd += kh * sn + kl * sn;
+        cap += c.dpi[s] * sn;
     }
 
     // 2. mixture velocity and temperature
-    const real ux0 = wx0 / w0, uy0 = wy0 / w0, ux1 = wx1 / w1, uy1 = wy1 / w1;
-    double T0d, T1d;
-    const real T0 = mixture_T(we0, w0, wd0, ux0, uy0, T0d);
-    const real T1 = mixture_T(we1, w1, wd1, ux1, uy1, T1d);
+    const float ux = wx / w, uy = wy / w;
+    double Td;
+    const float T = mixture_T(we, w, wd, ux, uy, Td);
 
     unsigned bad = 0;
-    real a0 = 0, a1 = 0;  // sum_s |n^s| of both cells
+    float a = 0;  // sum_s |n^s|
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        a0 += fabs(n0[s]);
-        a1 += fabs(n1[s]);
-    }
+    for (int s = 0; s < S; ++s) a += fabsf(n[s]);
 #pragma unroll
     for (int s = 0; s < S; ++s)
-        if (!(n0[s] >= real(-1e-6) * a0) || !(n1[s] >= real(-1e-6) * a1)) bad |= DBM_HEALTH_DENSITY;
-    if (!(a0 > real(0)) || !(a1 > real(0))) bad |= DBM_HEALTH_DENSITY;
-    if (!(T0 > real(0)) || !(T1 > real(0))) bad |= DBM_HEALTH_TEMPERATURE;
-    if (!isfinite(T0 + T1 + ux0 + uy0 + ux1 + uy1)) bad |= DBM_HEALTH_NONFINITE;
+        if (!(n[s] >= -1e-6f * a)) bad |= DBM_HEALTH_DENSITY;
+    if (!(a > 0.0f)) bad |= DBM_HEALTH_DENSITY;
+    if (!(T > 0.0f)) bad |= DBM_HEALTH_TEMPERATURE;
+    if (!isfinite(T + ux + uy)) bad |= DBM_HEALTH_NONFINITE;
 
     // 3. reaction: omega_ov and T' (state after a time tau^s), FP64
-    double om0 = 0.0, om1 = 0.0, dT0 = 0.0, dT1 = 0.0;
+    double om = 0.0, dT = 0.0;
     if (c.has_reaction) {
-        om0 = c.k_ov * (double)nf0 * (double)no0 * exp(-c.Ea_over_R / T0d);
-        om1 = c.k_ov * (double)nf1 * (double)no1 * exp(-c.Ea_over_R / T1d);
-        dT0 = (c.Qheat - 0.5 * T0d * c.src) * om0 / (0.5 * (double)cap0);
-        dT1 = (c.Qheat - 0.5 * T1d * c.src) * om1 / (0.5 * (double)cap1);
+        om = c.k_ov * (double)nf * (double)no * exp(-c.Ea_over_R / Td);
+        dT = (c.Qheat - 0.5 * Td * c.src) * om / (0.5 * (double)cap);
     }
 
-    Site w;
-    w.x0 = x0;
-    w.y = y;
-    w.two = two;
-    w.mx0 = ghost_mask(x0, c.nx, c.bc_x);
-    w.mx1 = two ? ghost_mask(x0 + 1, c.nx, c.bc_x) : 0u;
-    w.my = ghost_mask(y, c.ny, c.bc_y);
-    w.images = (w.mx0 | w.mx1 | w.my) != 0u;
-    w.cell = cell;
-    out.put_mix(w, ux0, uy0, T0, ux1, uy1, T1);
+    Site w_;
+    w_.x = x;
+    w_.y = y;
+    w_.mx = ghost_mask(x, c.nx, c.bc_x);
+    w_.my = ghost_mask(y, c.ny, c.bc_y);
+    w_.cell = (long long)(y + GY) * c.pitch + (x + GX);
+    const bool images = (w_.mx | w_.my) != 0u;
+    out.put_mix(w_, ux, uy, T);
 
 #pragma unroll 1
     for (int s = 0; s < S; ++s) {
-        // centres of this species, both cells
-        real f0[Q], f1[Q];
+        float f0[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const R2 v = t.ld(s * Q + i, 0, 0);
-            f0[i] = v.x;
-            f1[i] = v.y;
-        }
-        // 4. merged equilibrium moments of both cells
-        real cb0[16], cb1[16];
-        real ns0 = 0, ns1 = 0;
+        for (int i = 0; i < Q; ++i) f0[i] = t.ld(s * Q + i, 0, 0);
+        // species density from step 1 (selected, not indexed)
+        float ns = n[0];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            ns0 += f0[i];
-            ns1 += f1[i];
-        }
-        out.put_n(w, s, ns0, ns1);
+        for (int j = 1; j < S; ++j)
+            if (s == j) ns = n[j];
+        out.put_n(w_, s, ns);
+        // 4. merged equilibrium moments
+        float cb[16];
         {
-            real nr0 = ns0, nr1 = ns1;
-            real Ts0 = T0, Ts1 = T1;
+            float nr = ns, Ts = T;
             if (c.has_reaction) {
-                const double e0 = (double)ns0 + c.tau_a[s] * om0, e1 = (double)ns1 + c.tau_a[s] * om1;
-                if (e0 < -1e-6 * (double)a0 || e1 < -1e-6 * (double)a1) bad |= DBM_HEALTH_NSTAR;
-                nr0 = (real)e0;
-                nr1 = (real)e1;
-                Ts0 = (real)(T0d + c.tau_d[s] * dT0);
-                Ts1 = (real)(T1d + c.tau_d[s] * dT1);
+                const double e = (double)ns + c.tau_a[s] * om;
+                if (e < -1e-6 * (double)a) bad |= DBM_HEALTH_NSTAR;
+                nr = (float)e;
+                Ts = (float)(Td + c.tau_d[s] * dT);
             }
-            fhat_blocks<real>(nr0, ux0, uy0, Ts0 * c.inv_m[s], c.dpi[s], cb0);
-            fhat_blocks<real>(nr1, ux1, uy1, Ts1 * c.inv_m[s], c.dpi[s], cb1);
-            if (c.has_force) {
-                // species velocity and temperature from this species' moments
-                real jx0 = 0, jx1 = 0, jy0 = 0, jy1 = 0, e0 = 0, e1 = 0;
+            fhat_blocks<float>(nr, ux, uy, Ts * c.inv_m[s], c.dpi[s], cb);
+            if (c.has_force && ns != 0.0f) {  // an absent species feels no force
+                float jx = 0, jy = 0, e = 0;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    const real vx = dir_x(i) * c.vr[s][i >> 2], vy = dir_y(i) * c.vr[s][i >> 2];
-                    jx0 += vx * f0[i];
-                    jx1 += vx * f1[i];
-                    jy0 += vy * f0[i];
-                    jy1 += vy * f1[i];
-                    e0 += c.qr[s][i >> 2] * f0[i];
-                    e1 += c.qr[s][i >> 2] * f1[i];
+                    const float v = c.vr[s][i >> 2];
+                    jx += (dir_x(i) * v) * f0[i];
+                    jy += (dir_y(i) * v) * f0[i];
+                    e += c.qr[s][i >> 2] * f0[i];
                 }
-                real g[16], h[16];
-                if (ns0 != real(0)) {  // an absent species feels no force
-                    const real usx = jx0 / ns0, usy = jy0 / ns0;
-                    const real th = (e0 / ns0 - (usx * usx + usy * usy)) / c.dpi[s];
-                    fhat_blocks<real>(ns0, usx + c.accel_x * c.tau[s], usy + c.accel_y * c.tau[s], th,
-                                      c.dpi[s], g);
-                    fhat_blocks<real>(ns0, usx, usy, th, c.dpi[s], h);
+                const float usx = jx / ns, usy = jy / ns;
+                const float th = (e / ns - (usx * usx + usy * usy)) / c.dpi[s];
+                float g[16], h[16];
+                fhat_blocks<float>(ns, usx + c.accel_x * c.tau[s], usy + c.accel_y * c.tau[s], th, c.dpi[s], g);
+                fhat_blocks<float>(ns, usx, usy, th, c.dpi[s], h);
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) cb0[k] += g[k] - h[k];
-                }
-                if (ns1 != real(0)) {
-                    const real usx = jx1 / ns1, usy = jy1 / ns1;
-                    const real th = (e1 / ns1 - (usx * usx + usy * usy)) / c.dpi[s];
-                    fhat_blocks<real>(ns1, usx + c.accel_x * c.tau[s], usy + c.accel_y * c.tau[s], th,
-                                      c.dpi[s], g);
-                    fhat_blocks<real>(ns1, usx, usy, th, c.dpi[s], h);
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) cb1[k] += g[k] - h[k];
-                }
+                for (int k = 0; k < 16; ++k) cb[k] += g[k] - h[k];
             }
         }
-        real o0[16], o1[16];
-        solve_blocks<real, S>(c, s, cb0, o0);
-        solve_blocks<real, S>(c, s, cb1, o1);
-        const real dtt = c.dt_tau[s];
+        float o[16];
+        solve_blocks<float>(c, s, cb, o);
+        const float dtt = c.dt_tau[s];
 
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int p = s * Q + i;
-            const int r = i >> 2;
-            real d0 = 0, d1 = 0;  // dt * v . grad f of both cells
+            const int p = s * Q + i, r = i >> 2;
+            float d = 0;  // dt v . grad f
             // 5. NND advection
-            if (dir_x(i) != 0) {
-                const R2 L = t.ld(p, -2, 0), Rr = t.ld(p, 2, 0);
-                real e0, e1;
-                nnd_x_pair<real>(dir_x(i), L.x, L.y, f0[i], f1[i], Rr.x, Rr.y, e0, e1);
-                const real cx = dir_x(i) * c.cdx[s][r];
-                d0 += cx * e0;
-                d1 += cx * e1;
-            }
-            if (dir_y(i) > 0) {
-                const R2 m2 = t.ld(p, 0, -2), m1 = t.ld(p, 0, -1), p1 = t.ld(p, 0, 1);
-                const real cy = c.cdy[s][r];
-                d0 += cy * nnd_diff_pos(m2.x, m1.x, f0[i], p1.x);
-                d1 += cy * nnd_diff_pos(m2.y, m1.y, f1[i], p1.y);
-            } else if (dir_y(i) < 0) {
-                const R2 m1 = t.ld(p, 0, -1), p1 = t.ld(p, 0, 1), p2 = t.ld(p, 0, 2);
-                const real cy = c.cdy[s][r];
-                d0 -= cy * nnd_diff_neg(m1.x, f0[i], p1.x, p2.x);
-                d1 -= cy * nnd_diff_neg(m1.y, f1[i], p1.y, p2.y);
-            }
+            if (dir_x(i) > 0)
+                d += c.cdx[s][r] * nnd_diff_pos(t.ld(p, -2, 0), t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0));
+            else if (dir_x(i) < 0)
+                d -= c.cdx[s][r] * nnd_diff_neg(t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0), t.ld(p, 2, 0));
+            if (dir_y(i) > 0)
+                d += c.cdy[s][r] * nnd_diff_pos(t.ld(p, 0, -2), t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1));
+            else if (dir_y(i) < 0)
+                d -= c.cdy[s][r] * nnd_diff_neg(t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1), t.ld(p, 0, 2));
             // 6. forward Euler: f + dt/tau (f^eq,tot - f) - dt v . grad f
-            const real e0 = feq_of<real>(i, o0), e1 = feq_of<real>(i, o1);
-            const real g0 = f0[i] + dtt * (e0 - f0[i]) - d0;
-            const real g1 = f1[i] + dtt * (e1 - f1[i]) - d1;
-            out.put(w, p, g0, g1, e0, e1);
+            const float e = feq_of<float>(i, o);
+            out.put(w_, p, f0[i] + dtt * (e - f0[i]) - d, e);
         }
+        if (images) out.images(w_, s);
     }
+    if (images) out.images_mix(w_);
     if (bad) raise_flag(flag, bad);
 }
 
 // Generic kernel: inputs from global memory through the read-only path.
-template <typename real, int S>
-__global__ void __launch_bounds__(256, 2)
-    k_step(const __grid_constant__ StepConsts<real, S> c, const real *__restrict__ fin,
-           real *__restrict__ fout, unsigned *__restrict__ flag)
+template <int S>
+__global__ void __launch_bounds__(256)
+    k_step(const __grid_constant__ StepConsts<float, S> c, const float *__restrict__ fin, float *__restrict__ fout,
+           unsigned *__restrict__ flag)
 {
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x0 >= c.nx || y >= c.ny) return;
-    GlobalTile<real> t;
-    t.base = fin + (long long)(y + GY) * c.pitch + (x0 + GX);
+    if (x >= c.nx || y >= c.ny) return;
+    GlobalTile t;
+    t.base = fin + (long long)(y + GY) * c.pitch + (x + GX);
     t.P = c.plane;
     t.py = c.pitch;
-    StateOut<real> o{fout, c.plane, c.nx, c.ny, c.pitch};
-    step_pair<real, S>(c, t, x0, y, o, flag);
+    StateOut o{fout, c.plane, c.nx, c.ny, c.pitch};
+    step_cell<S>(c, t, x, y, o, flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -523,16 +404,29 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long lo
 
 constexpr long long TMA_WAIT_LIMIT = 1LL << 22;  // try_wait polls (each may suspend ~us)
 
-template <typename real, int S, int TX, int TY>
-__global__ void __launch_bounds__((TX / 2) * TY, 2)
-    k_step_tma(const __grid_constant__ StepConsts<real, S> c, const __grid_constant__ CUtensorMap tmap,
-               real *__restrict__ fout, unsigned *__restrict__ flag)
+// Issue the tile copy (leader thread): box origin column bx0 (= bx0 + GX - 4),
+// row by0 (= by0 + GY - 2), plane 0.
+__device__ __forceinline__ void tma_tile_load(float *tile, unsigned long long tmap, int bx0, int by0,
+                                              unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(tile)),
+        "l"(tmap), "r"(bx0), "r"(by0), "r"(0), "r"(bar)
+        : "memory");
+}
+
+template <int S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, 2)
+    k_step_tma(const __grid_constant__ StepConsts<float, S> c, const __grid_constant__ CUtensorMap tmap,
+               float *__restrict__ fout, unsigned *__restrict__ flag)
 {
     constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q;
-    constexpr unsigned BYTES = (unsigned)(BX * BY * NP * sizeof(real));
+    constexpr unsigned BYTES = (unsigned)(BX * BY * NP * sizeof(float));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
-    real *tile = reinterpret_cast<real *>(smem_raw);
+    float *tile = reinterpret_cast<float *>(smem_raw);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool leader = tx == 0 && ty == 0;
     const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
@@ -542,15 +436,7 @@ __global__ void __launch_bounds__((TX / 2) * TY, 2)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (leader) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(BYTES) : "memory");
-        // box origin: column (bx0 + GX) - 4 = bx0, row (by0 + GY) - 2 = by0, plane 0
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(tile)),
-            "l"(reinterpret_cast<unsigned long long>(&tmap)), "r"(bx0), "r"(by0), "r"(0), "r"(b)
-            : "memory");
-    }
+    if (leader) tma_tile_load(tile, reinterpret_cast<unsigned long long>(&tmap), bx0, by0, b, BYTES);
     if (!mbar_wait(b, 0, TMA_WAIT_LIMIT)) {
         // the copy did not land: report, give it one more bounded wait so
         // that no copy is left writing into this block's shared memory, leave
@@ -558,43 +444,43 @@ __global__ void __launch_bounds__((TX / 2) * TY, 2)
         mbar_wait(b, 0, TMA_WAIT_LIMIT);
         return;
     }
-    const int x0 = bx0 + 2 * tx, y = by0 + ty;
-    if (x0 >= c.nx || y >= c.ny) return;
-    SmemTile<real> t;
-    t.base = tile + (ty + 2) * BX + (2 * tx + 4);
+    const int x = bx0 + tx, y = by0 + ty;
+    if (x >= c.nx || y >= c.ny) return;
+    SmemTile t;
+    t.base = tile + (ty + 2) * BX + (tx + 4);
     t.P = BY * BX;
     t.py = BX;
-    StateOut<real> o{fout, c.plane, c.nx, c.ny, c.pitch};
-    step_pair<real, S>(c, t, x0, y, o, flag);
+    StateOut o{fout, c.plane, c.nx, c.ny, c.pitch};
+    step_cell<S>(c, t, x, y, o, flag);
 }
 
-template <typename real, int S>
+template <int S>
 int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st)
 {
-    StepConsts<real, S> c;
-    fill_step_consts<real, S>(h, c);
-    dim3 block(32, 8);
-    dim3 grid((h->p.nx + 63) / 64, (h->p.ny + 7) / 8);
-    k_step<real, S><<<grid, block, 0, st>>>(c, (const real *)fin, (real *)fout, (unsigned *)h->scratch);
+    StepConsts<float, S> c;
+    fill_step_consts<float, S>(h, c);
+    dim3 block(64, 4);
+    dim3 grid((h->p.nx + 63) / 64, (h->p.ny + 3) / 4);
+    k_step<S><<<grid, block, 0, st>>>(c, (const float *)fin, (float *)fout, (unsigned *)h->scratch);
     return set_cuda_error(h, cudaGetLastError(), "step kernel launch");
 }
 
-template <typename real, int S, int TX, int TY>
+template <int S, int TX, int TY>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, void *fout, cudaStream_t st)
 {
-    constexpr size_t smem = (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(real);
+    constexpr size_t smem = (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float);
     static bool attr_set = false;  // per instantiation, set once per process
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_tma<real, S, TX, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_step_tma<S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return set_cuda_error(h, e, "TMA step kernel shared-memory attribute");
         attr_set = true;
     }
-    StepConsts<real, S> c;
-    fill_step_consts<real, S>(h, c);
-    dim3 block(TX / 2, TY);
+    StepConsts<float, S> c;
+    fill_step_consts<float, S>(h, c);
+    dim3 block(TX, TY);
     dim3 grid((h->p.nx + TX - 1) / TX, (h->p.ny + TY - 1) / TY);
-    k_step_tma<real, S, TX, TY><<<grid, block, smem, st>>>(c, *tmap, (real *)fout, (unsigned *)h->scratch);
+    k_step_tma<S, TX, TY><<<grid, block, smem, st>>>(c, *tmap, (float *)fout, (unsigned *)h->scratch);
     return set_cuda_error(h, cudaGetLastError(), "TMA step kernel launch");
 }
 

@@ -2,6 +2,6 @@
 #include "dbm_step_impl.cuh"
 
 namespace dbm {
-template int launch_step_t<float, 1>(dbm_handle *, const void *, void *, cudaStream_t);
-template int launch_step_tma_t<float, 1, 64, 8>(dbm_handle *, const CUtensorMap *, void *, cudaStream_t);
+template int launch_step_t<1>(dbm_handle *, const void *, void *, cudaStream_t);
+template int launch_step_tma_t<1, 64, 8>(dbm_handle *, const CUtensorMap *, void *, cudaStream_t);
 }  // namespace dbm

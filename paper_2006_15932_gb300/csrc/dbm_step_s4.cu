@@ -2,5 +2,5 @@
 #include "dbm_step_impl.cuh"
 
 namespace dbm {
-template int launch_step_t<float, 4>(dbm_handle *, const void *, void *, cudaStream_t);
+template int launch_step_t<4>(dbm_handle *, const void *, void *, cudaStream_t);
 }  // namespace dbm

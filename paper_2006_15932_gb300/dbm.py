@@ -39,7 +39,8 @@ EXPORTS = [
     "dbm_init", "dbm_init_error", "dbm_equilibrium_matrix", "dbm_get_layout", "dbm_state_bytes", "dbm_scratch_bytes",
     "dbm_bind", "dbm_set_state", "dbm_set_f", "dbm_get_f", "dbm_step", "dbm_moments",
     "dbm_nonequilibrium", "dbm_conservation", "dbm_conservation_noalloc", "dbm_status", "dbm_steps_taken",
-    "dbm_last_error", "dbm_destroy",
+    "dbm_last_error", "dbm_destroy", "dbm_batch_table_bytes", "dbm_batch_create", "dbm_batch_tune",
+    "dbm_batch_step", "dbm_batch_info", "dbm_batch_last_error", "dbm_batch_destroy",
 ]
 
 
@@ -130,6 +131,16 @@ def load(path: str = LIB_PATH):
     L.dbm_last_error.restype = C.c_char_p
     L.dbm_destroy.argtypes = [H]
     L.dbm_destroy.restype = None
+    HP = C.POINTER(C.c_void_p)
+    L.dbm_batch_table_bytes.argtypes = [HP, C.c_int, C.POINTER(C.c_size_t)]
+    L.dbm_batch_create.argtypes = [HP, C.c_int, vp, C.c_size_t, vp, C.POINTER(C.c_void_p)]
+    L.dbm_batch_tune.argtypes = [vp, vp, C.c_int]
+    L.dbm_batch_step.argtypes = [vp, C.c_int, vp]
+    L.dbm_batch_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
+    L.dbm_batch_last_error.argtypes = [vp]
+    L.dbm_batch_last_error.restype = C.c_char_p
+    L.dbm_batch_destroy.argtypes = [vp]
+    L.dbm_batch_destroy.restype = None
     for name in EXPORTS:
         getattr(L, name)
     _lib = L
@@ -361,6 +372,89 @@ class Solver:
         if self.h:
             dbm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+
+def _bcheck(b, rc):
+    if rc != OK:
+        raise DbmError(rc, load().dbm_batch_last_error(b).decode() if b else "")
+
+
+def dbm_batch_table_bytes(handles) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    v = C.c_size_t()
+    rc = load().dbm_batch_table_bytes(arr, len(handles), C.byref(v))
+    if rc != OK:
+        raise DbmError(rc, "batch: handles must be bound FP32 handles with the same S <= 3")
+    return v.value
+
+
+def dbm_batch_create(handles, table: int, table_bytes: int, stream: int = 0) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    b = C.c_void_p()
+    rc = load().dbm_batch_create(arr, len(handles), table, table_bytes, stream, C.byref(b))
+    if rc != OK:
+        raise DbmError(rc, "batch: handles must be bound FP32 handles with the same S <= 3")
+    return b.value
+
+
+def dbm_batch_tune(b, stream: int = 0, reps: int = 3) -> None:
+    _bcheck(b, load().dbm_batch_tune(b, stream, reps))
+
+
+def dbm_batch_step(b, nsteps: int, stream: int = 0) -> None:
+    _bcheck(b, load().dbm_batch_step(b, int(nsteps), stream))
+
+
+def dbm_batch_info(b) -> dict:
+    v = [C.c_int() for _ in range(4)]
+    _bcheck(b, load().dbm_batch_info(b, *[C.byref(x) for x in v]))
+    return {"tile": (v[0].value, v[1].value), "tiles": v[2].value, "ctas": v[3].value}
+
+
+def dbm_batch_destroy(b) -> None:
+    load().dbm_batch_destroy(b)
+
+
+class Batch:
+    """Solvers (FP32, same species count) stepped together by one persistent
+    launch per step, replayed from CUDA graphs on the solvers' stream."""
+
+    def __init__(self, solvers, stream=None, tune=True):
+        import torch
+
+        self.torch = torch
+        self.solvers = list(solvers)
+        dev = self.solvers[0].device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        handles = [s.h for s in self.solvers]
+        nb = dbm_batch_table_bytes(handles)
+        self.table = torch.empty(nb + 128, dtype=torch.uint8, device=dev)
+        base = self.table.data_ptr()
+        self._tp = (base + 127) // 128 * 128
+        self.b = dbm_batch_create(handles, self._tp, nb, self.stream.cuda_stream)
+        if tune:
+            dbm_batch_tune(self.b, self.stream.cuda_stream)
+
+    def step(self, nsteps: int):
+        dbm_batch_step(self.b, nsteps, self.stream.cuda_stream)
+
+    def info(self) -> dict:
+        return dbm_batch_info(self.b)
+
+    def close(self):
+        if self.b:
+            dbm_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

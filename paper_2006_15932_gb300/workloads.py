@@ -215,3 +215,55 @@ def uniform(nx: int, ny: int, sp: List[SpeciesSpec], rho_s, ux=0.0, uy=0.0, T=1.
     return Problem(name=f"uniform_{nx}x{ny}", nx=nx, ny=ny, species=sp, rho_s=rho_s,
                    ux=np.full((ny, nx), float(ux)), uy=np.full((ny, nx), float(uy)),
                    T=np.full((ny, nx), float(T)), **kw)
+
+
+def shock_instance(L: int, seed: int) -> Problem:
+    """An L x L two-species Sod-type tube along x (the shock-tube states:
+    rho = 1, p = 1 left of x = L/2, rho = 0.125, p = 0.1 right), with a
+    small seeded transverse perturbation of the interface so that the
+    instance is genuinely 2-D; outflow in x, periodic in y."""
+    rng = np.random.default_rng(seed)
+    ph = float(rng.uniform(0, 2 * math.pi))
+    x = np.arange(L)[None, :] * np.ones((L, 1))
+    y = np.arange(L)[:, None] * np.ones((1, L))
+    x0 = L / 2 + 2.0 * np.sin(2 * math.pi * y / L + ph)
+    left = x < x0
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    sp = [species(tau=2e-5), species(tau=2e-5)]
+    return Problem(name=f"shock_{L}", nx=L, ny=L, species=sp, dx=1e-3, dy=1e-3, dt=1e-5, bc_x=OUTFLOW,
+                   bc_y=PERIODIC, rho_s=np.stack([0.5 * rho, 0.5 * rho]), ux=np.zeros((L, L)),
+                   uy=np.zeros((L, L)), T=p / rho)
+
+
+def reactive_instance(L: int, seed: int) -> Problem:
+    """An L x L two-species reactive gas, F -> P (a = -1, +1, m = 1 each,
+    rate k n_F n_F exp(-E_a/T): fuel and oxidiser index the same species),
+    premixed fuel at T = 1 with a hot product spot at the centre; seeded
+    k_ov, E_a/R, Q; periodic in x and y."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    r2 = ((xx - L / 2) ** 2 + (yy - L / 2) ** 2) / (L / 8) ** 2
+    hot = np.exp(-r2)
+    yF = 0.95 - 0.9 * hot
+    rho = np.ones((L, L))
+    T = 1.0 + 0.8 * hot
+    sp = [species(tau=2e-5, a=-1.0), species(tau=2e-5, a=1.0)]
+    return Problem(name=f"reactive_{L}", nx=L, ny=L, species=sp, dx=1e-3, dy=1e-3, dt=1e-5, bc_x=PERIODIC,
+                   bc_y=PERIODIC, fuel=0, oxid=0, k_ov=float(rng.uniform(20.0, 40.0)),
+                   Ea_over_R=float(rng.uniform(2.0, 3.0)), Q=float(rng.uniform(0.3, 0.6)),
+                   rho_s=np.stack([rho * yF, rho * (1.0 - yF)]), ux=np.zeros((L, L)), uy=np.zeros((L, L)), T=T)
+
+
+def batched_instances(n: int = 64, seed: int = SEED, lo: int = 64, hi: int = 512):
+    """The batched workload: n independent two-species instances, sides
+    drawn uniformly in [lo, hi] from the seed, alternately shock tubes and
+    reactive gases; each also gets a seeded step count in [1000, 2000]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        L = int(rng.integers(lo, hi + 1))
+        pb = shock_instance(L, seed + k) if k % 2 == 0 else reactive_instance(L, seed + k)
+        pb.nsteps = int(rng.integers(1000, 2001))
+        out.append(pb)
+    return out

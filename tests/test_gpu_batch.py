@@ -1,0 +1,117 @@
+"""Batched stepping (dbm_batch_*): many independent FP32 problems advanced
+by one persistent launch per step, replayed from CUDA graphs."""
+import numpy as np
+import pytest
+
+from paper_2006_15932_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_15932_gb300 import build as B
+    from paper_2006_15932_gb300 import dbm
+
+    B.build()
+    dbm.load()
+    return dbm
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _mixed(n=8, seed=3):
+    return W.batched_instances(n, seed=seed, lo=21, hi=140)
+
+
+def test_batch_matches_individual_steps(D):
+    pbs = _mixed()
+    stream = torch.cuda.Stream()
+    solo, mixed = [], []
+    for pb in pbs:
+        for group in (solo, mixed):
+            s = D.Solver(pb, "fp32", stream=stream)
+            s.set_state()
+            group.append(s)
+    for s in solo:
+        s.step(21)
+    batch = D.Batch(mixed, stream=stream)
+    batch.step(21)  # 10 graph pairs + 1 single step
+    torch.cuda.synchronize()
+    for a, b in zip(solo, mixed):
+        assert b.status()[0] == 0
+        assert D.dbm_steps_taken(b.h) == 21
+        fa, fb = a.get_f().cpu().numpy(), b.get_f().cpu().numpy()
+        assert rel(fb, fa) <= 1e-6
+
+
+def test_batch_tune_leaves_states_unchanged(D):
+    pbs = _mixed(6, seed=5)
+    stream = torch.cuda.Stream()
+    sols = []
+    for pb in pbs:
+        s = D.Solver(pb, "fp32", stream=stream)
+        s.set_state()
+        s.step(3)
+        sols.append(s)
+    before = [s.get_f().cpu().numpy() for s in sols]
+    batch = D.Batch(sols, stream=stream, tune=True)
+    info = batch.info()
+    assert info["tile"] in ((64, 8), (32, 8), (32, 16)) and info["tiles"] > 0
+    after = [s.get_f().cpu().numpy() for s in sols]
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+
+
+def test_batch_against_oracle(D, orc):
+    pbs = [W.shock_instance(24, 1), W.reactive_instance(19, 2), W.shock_instance(33, 3)]
+    stream = torch.cuda.Stream()
+    sols = []
+    for pb in pbs:
+        s = D.Solver(pb, "fp32", stream=stream)
+        s.set_state()
+        sols.append(s)
+    batch = D.Batch(sols, stream=stream)
+    batch.step(30)
+    torch.cuda.synchronize()
+    for pb, s in zip(pbs, sols):
+        p = W.to_oracle_params(pb)
+        f0 = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
+        fr, st = orc.run(p, f0, 30)
+        assert st == 0
+        assert rel(s.get_f().cpu().numpy(), fr) <= 2e-5
+
+
+def test_batch_picks_up_a_reset_handle(D):
+    pbs = _mixed(4, seed=9)
+    stream = torch.cuda.Stream()
+    sols, ref = [], []
+    for pb in pbs:
+        for group in (sols, ref):
+            s = D.Solver(pb, "fp32", stream=stream)
+            s.set_state()
+            group.append(s)
+    batch = D.Batch(sols, stream=stream, tune=False)
+    batch.step(5)
+    sols[1].set_state()  # restart one instance from its initial fields
+    batch.step(4)
+    for k, s in enumerate(ref):
+        s.step(4 if k == 1 else 9)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, sols):
+        assert rel(b.get_f().cpu().numpy(), a.get_f().cpu().numpy()) <= 1e-6
+
+
+def test_batch_rejects_mixed_species_or_precision(D):
+    stream = torch.cuda.Stream()
+    a = D.Solver(W.random_smooth(16, 8, 2), "fp32", stream=stream)
+    b = D.Solver(W.random_smooth(16, 8, 3), "fp32", stream=stream)
+    c = D.Solver(W.random_smooth(16, 8, 2), "fp64", stream=stream)
+    for group in ([a, b], [a, c]):
+        with pytest.raises(D.DbmError):
+            D.Batch(group, stream=stream)
