@@ -284,12 +284,15 @@ def main():
                "grids": "square, sides uniform in [64, 512] (seeded)", "species": 2, "velocities": 16,
                "precision": args.precision, "cells": sum(q.nx * q.ny for q in pbs),
                "l2_policy": "inputs larger than L2",
-               "launch": "one persistent launch per step, pairs of steps replayed from a CUDA graph"}
+               "launch": "one launch per step over all instances' tiles, pairs of steps replayed from a CUDA graph"}
         solvers = [D.Solver(q, args.precision, device=dev, stream=stream) for q in pbs]
         for s_ in solvers:
             s_.set_state()
         batch = D.Batch(solvers, stream=stream, tune=True)
-        cfg["tile"] = list(batch.info()["tile"])
+        info = batch.info()
+        cfg["tile"] = list(info["tile"])
+        cfg["ctas_per_launch"] = info["ctas"]
+        cfg["tiles_per_step"] = info["tiles"]
         units = sum(q.nx * q.ny * q.ns for q in pbs)
         per_call = 2  # one graph replay = two steps
 

@@ -207,9 +207,10 @@ int dbm_conservation(dbm_handle *h, double *out, void *stream);
  *
  * A batch groups bound FP32 handles with the same species count S <= 3
  * (grids, boundaries, species constants, reaction and time step may all
- * differ).  Each dbm_batch_step advances every instance: one persistent
- * kernel launch per time step walks the tiles of all instances, each tile
- * staged by TMA through its instance's own descriptor; pairs of steps are
+ * differ).  Each dbm_batch_step advances every instance: one kernel launch
+ * per time step covers the tiles of all instances (each CTA a contiguous
+ * range of tiles, or one tile per CTA), each tile staged by TMA through its
+ * instance's own descriptor; pairs of steps are
  * replayed from captured CUDA graphs when `stream` is a created stream.
  * The caller owns the device table (dbm_batch_table_bytes, 128-byte
  * aligned).  While a batch exists, step its handles through it; a handle
@@ -226,16 +227,18 @@ int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes);
 int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t table_bytes, void *stream,
                      dbm_batch **out);
 
-/* Choose the tile shape (64x8, 32x8 or 32x16 cells) that steps this batch
- * fastest: each shape is timed on `reps` trial launches that read the
- * current states and write only the buffers the next step overwrites, so
- * no state advances.  Synchronises the stream. */
+/* Choose the tile shape (64x8, 32x8 or 32x16 cells) and the launch form
+ * (as many CTAs as are resident at once, each walking a contiguous range
+ * of tiles, or one CTA per tile) that step this batch fastest: each pair
+ * is timed on `reps` trial launches that read the current states and write
+ * only the buffers the next step overwrites, so no state advances.
+ * Synchronises the stream. */
 int dbm_batch_tune(dbm_batch *b, void *stream, int reps);
 
 /* Advance every instance of the batch by nsteps >= 0 (async on stream). */
 int dbm_batch_step(dbm_batch *b, int nsteps, void *stream);
 
-/* Current tile shape, number of tiles per step and persistent CTAs. */
+/* Current tile shape, number of tiles per step and CTAs per launch. */
 int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int *ctas);
 
 const char *dbm_batch_last_error(const dbm_batch *b);

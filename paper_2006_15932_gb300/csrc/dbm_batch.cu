@@ -3,11 +3,11 @@
 // A batch groups bound FP32 handles with the same species count.  One
 // persistent kernel launch per time step walks the tiles of every instance
 // (instances may differ in grid size, boundaries, species constants,
-// reaction and time step): per tile it finds the instance by binary search
-// over the tile prefix sums, copies that instance's step constants into
-// shared memory, stages the tile plus halo with one TMA copy through the
-// instance's own tensor map, and runs the same per-pair arithmetic as the
-// single-problem kernel.  Steps are replayed from captured CUDA graphs, and
+// reaction and time step): each CTA takes a contiguous range of tiles, looks
+// up each tile's instance in a table, copies that instance's step constants
+// into shared memory when the instance changes, stages the tile plus halo
+// with one TMA copy through the instance's own tensor map, and runs the
+// same per-cell arithmetic as the single-problem kernel.  Steps are replayed from captured CUDA graphs, and
 // the tile shape is chosen by timing each compiled shape (dbm_batch_tune).
 #include <stdio.h>
 #include <stdlib.h>
@@ -31,15 +31,13 @@ struct __align__(128) BatchEntry {
 
 template <int S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, 2)
-    k_step_batch(const BatchEntry<S> *__restrict__ tab, const int *__restrict__ prefix, int n, int total,
-                 int parity)
+    k_step_batch(const BatchEntry<S> *__restrict__ tab, const int *__restrict__ tile_inst, int total, int parity)
 {
     constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q;
     constexpr unsigned BYTES = (unsigned)(BX * BY * NP * sizeof(float));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
     __shared__ StepConsts<float, S> sc;
-    __shared__ int s_k;
     float *tile = reinterpret_cast<float *>(smem_raw);
     const int tx = threadIdx.x, ty = threadIdx.y, nthr = TX * TY, tid = ty * TX + tx;
     const bool leader = tid == 0;
@@ -48,21 +46,16 @@ __global__ void __launch_bounds__(TX *TY, 2)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // a contiguous range of tiles per CTA: consecutive tiles mostly belong
+    // to the same instance, so its constants stay in shared memory
+    const int t0 = (int)((long long)total * blockIdx.x / gridDim.x);
+    const int t1 = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
     int k_loaded = -1;
     unsigned phase = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, phase ^= 1u) {
-        if (leader) {  // instance of tile t: largest k with prefix[k] <= t
-            int lo = 0, hi = n - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (prefix[mid] <= t) lo = mid;
-                else hi = mid - 1;
-            }
-            s_k = lo;
-        }
-        __syncthreads();  // also: the previous tile is finished with the shared tile
-        const int k = s_k;
+    for (int t = t0; t < t1; ++t, phase ^= 1u) {
+        const int k = tile_inst[t];
         const BatchEntry<S> &e = tab[k];
+        __syncthreads();  // the previous tile is done with the shared tile and constants
         const int local = t - e.tile_begin;
         const int bx0 = (local % e.tiles_x) * TX, by0 = (local / e.tiles_x) * TY;
         if (leader) {
@@ -76,8 +69,8 @@ __global__ void __launch_bounds__(TX *TY, 2)
             unsigned *dst = reinterpret_cast<unsigned *>(&sc);
             for (int j = tid; j < (int)(sizeof(sc) / 4); j += nthr) dst[j] = src[j];
             k_loaded = k;
+            __syncthreads();
         }
-        __syncthreads();
         if (!mbar_wait(b, phase, TMA_WAIT_LIMIT)) {
             if (leader) raise_flag(e.flag, DBM_HEALTH_TIMEOUT);
             mbar_wait(b, phase, TMA_WAIT_LIMIT);
@@ -113,6 +106,7 @@ struct dbm_batch {
     std::vector<dbm_handle *> h;
     int S;
     int shape;                 // index into SHAPE_TX / SHAPE_TY
+    int persistent;            // 1: as many CTAs as fit at once; 0: one CTA per tile
     int parity;                // steps taken mod 2
     int total_tiles, ctas;
     void *table;               // caller's device buffer
@@ -136,10 +130,26 @@ static size_t entry_bytes()
     return sizeof(BatchEntry<S>);
 }
 
-static size_t table_size(int S, int n)
+// Tiles per step of these handles with a TX x TY tile.
+static long long count_tiles(dbm_handle *const *h, int n, int TX, int TY)
 {
+    long long t = 0;
+    for (int k = 0; k < n; ++k) t += (long long)((h[k]->p.nx + TX - 1) / TX) * ((h[k]->p.ny + TY - 1) / TY);
+    return t;
+}
+
+// Table: n entries, then the instance of every tile (for the tile shape
+// with the most tiles).
+static size_t table_size(dbm_handle *const *h, int n)
+{
+    const int S = h[0]->p.nspecies;
     const size_t e = S == 1 ? entry_bytes<1>() : S == 2 ? entry_bytes<2>() : entry_bytes<3>();
-    return e * n + (size_t)(n + 1) * sizeof(int) + 256;
+    long long most = 0;
+    for (int sh = 0; sh < N_SHAPES; ++sh) {
+        const long long t = count_tiles(h, n, SHAPE_TX[sh], SHAPE_TY[sh]);
+        if (t > most) most = t;
+    }
+    return e * n + (size_t)most * sizeof(int) + 256;
 }
 
 template <int S>
@@ -153,7 +163,7 @@ static int write_table(dbm_batch *b, cudaStream_t st)
         q != cudaDriverEntryPointSuccess || !fn)
         return bfail(b, DBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     encode_tiled_fn_b encode = (encode_tiled_fn_b)fn;
-    const size_t bytes = table_size(S, n);
+    const size_t bytes = table_size(b->h.data(), n);
     if (b->host_bytes < bytes) {
         free(b->host);
         b->host = (unsigned char *)aligned_alloc(128, (bytes + 127) / 128 * 128);
@@ -163,7 +173,7 @@ static int write_table(dbm_batch *b, cudaStream_t st)
     memset(b->host, 0, bytes);
     b->expected_steps.assign(n, 0);
     BatchEntry<S> *ent = reinterpret_cast<BatchEntry<S> *>(b->host);
-    int *prefix = reinterpret_cast<int *>(b->host + sizeof(BatchEntry<S>) * n);
+    int *tile_inst = reinterpret_cast<int *>(b->host + sizeof(BatchEntry<S>) * n);
     int tiles = 0;
     for (int k = 0; k < n; ++k) {
         dbm_handle *h = b->h[k];
@@ -187,10 +197,10 @@ static int write_table(dbm_batch *b, cudaStream_t st)
         e.flag = (unsigned *)h->scratch;
         e.tiles_x = (h->p.nx + TX - 1) / TX;
         e.tile_begin = tiles;
-        prefix[k] = tiles;
-        tiles += e.tiles_x * ((h->p.ny + TY - 1) / TY);
+        const int nt = e.tiles_x * ((h->p.ny + TY - 1) / TY);
+        for (int j = 0; j < nt; ++j) tile_inst[tiles + j] = k;
+        tiles += nt;
     }
-    prefix[n] = tiles;
     b->total_tiles = tiles;
     // the table is rewritten while its parity layout is "current input at parity 0"
     cudaError_t er = cudaMemcpyAsync(b->table, b->host, bytes, cudaMemcpyHostToDevice, st);
@@ -198,6 +208,11 @@ static int write_table(dbm_batch *b, cudaStream_t st)
     er = cudaStreamSynchronize(st);  // the staging buffer may change on the next write
     if (er != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(er));
     return DBM_OK;
+}
+
+static int grid_size(const dbm_batch *b)
+{
+    return b->persistent && b->ctas < b->total_tiles ? b->ctas : b->total_tiles;
 }
 
 template <int S, int TX, int TY>
@@ -217,9 +232,9 @@ static int launch_batch_t(dbm_batch *b, int parity, cudaStream_t st, bool set_at
     }
     const int n = (int)b->h.size();
     const BatchEntry<S> *tab = reinterpret_cast<const BatchEntry<S> *>(b->table);
-    const int *prefix = reinterpret_cast<const int *>((const char *)b->table + sizeof(BatchEntry<S>) * n);
-    const int grid = b->total_tiles < b->ctas ? b->total_tiles : b->ctas;
-    k_step_batch<S, TX, TY><<<grid, dim3(TX, TY), smem, st>>>(tab, prefix, n, b->total_tiles, parity);
+    const int *tile_inst = reinterpret_cast<const int *>((const char *)b->table + sizeof(BatchEntry<S>) * n);
+    const int grid = grid_size(b);
+    k_step_batch<S, TX, TY><<<grid, dim3(TX, TY), smem, st>>>(tab, tile_inst, b->total_tiles, parity);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DBM_OK : bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
 }
@@ -265,7 +280,9 @@ int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes)
     if (!handles || n < 1 || !bytes || !handles[0]) return DBM_ERR_INVALID;
     const int S = handles[0]->p.nspecies;
     if (S > 3) return DBM_ERR_INVALID;
-    *bytes = table_size(S, n);
+    for (int k = 0; k < n; ++k)
+        if (!handles[k]) return DBM_ERR_INVALID;
+    *bytes = table_size(handles, n);
     return DBM_OK;
 }
 
@@ -280,13 +297,14 @@ int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t tabl
         if (!h || !h->bound || h->p.precision != DBM_FP32 || h->p.nspecies != S || S > 3 || !h->tma_ok)
             return DBM_ERR_INVALID;
     }
-    if (table_bytes < table_size(S, n) || ((uintptr_t)table & 127)) return DBM_ERR_INVALID;
+    if (table_bytes < table_size(handles, n) || ((uintptr_t)table & 127)) return DBM_ERR_INVALID;
     dbm_batch *b = new dbm_batch();
     b->host = nullptr;
     b->host_bytes = 0;
     b->h.assign(handles, handles + n);
     b->S = S;
     b->shape = 0;
+    b->persistent = 1;
     b->table = table;
     b->table_bytes = table_bytes;
     b->graph[0] = b->graph[1] = nullptr;
@@ -317,12 +335,14 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
     cudaStream_t st = (cudaStream_t)stream;
     if (reps < 1) reps = 3;
     float best = 1e30f;
-    int best_shape = 0;
+    int best_shape = 0, best_mode = 1;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int sh = 0; sh < N_SHAPES; ++sh) {
+    for (int trial = 0; trial < 2 * N_SHAPES; ++trial) {
+        const int sh = trial >> 1;
         b->shape = sh;
+        b->persistent = trial & 1;
         int rc = rebuild(b, st);
         // a trial launch reads the current states and writes the other
         // buffers, which the next real step overwrites: no state advances
@@ -343,11 +363,13 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
         if (ms < best) {
             best = ms;
             best_shape = sh;
+            best_mode = b->persistent;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->shape = best_shape;
+    b->persistent = best_mode;
     return rebuild(b, st);
 }
 
@@ -405,7 +427,7 @@ int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int
     if (tile_x) *tile_x = SHAPE_TX[b->shape];
     if (tile_y) *tile_y = SHAPE_TY[b->shape];
     if (tiles) *tiles = b->total_tiles;
-    if (ctas) *ctas = b->ctas;
+    if (ctas) *ctas = grid_size(b);
     return DBM_OK;
 }
 

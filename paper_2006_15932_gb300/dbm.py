@@ -300,6 +300,7 @@ class Solver:
         self.scratch = torch.zeros(ns, dtype=torch.uint8, device=self.device)
         dbm_bind(self.h, self.buf[0].data_ptr(), self.buf[1].data_ptr(), self.scratch.data_ptr())
         self.stream = stream
+        self._uses(*self.buf, self.scratch)
 
     @property
     def S(self) -> int:
@@ -310,9 +311,26 @@ class Solver:
         return self.pb.nx * self.pb.ny
 
     def _st(self) -> int:
+        """The stream the library works on.  With a stream of its own, the
+        solver first waits for the caller's current stream (inputs it
+        prepared) and the caller's stream waits for the solver's work before
+        it reads any output (see _join)."""
         torch = self.torch
-        s = self.stream if self.stream is not None else torch.cuda.current_stream(self.device)
-        return s.cuda_stream
+        if self.stream is None:
+            return torch.cuda.current_stream(self.device).cuda_stream
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        return self.stream.cuda_stream
+
+    def _uses(self, *tensors):
+        # memory that the solver's own stream reads or writes is not handed
+        # back to the allocator before that stream's work is done
+        if self.stream is not None:
+            for t in tensors:
+                t.record_stream(self.stream)
+
+    def _join(self):
+        if self.stream is not None:
+            self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
 
     def _dev(self, a):
         torch = self.torch
@@ -328,18 +346,21 @@ class Solver:
         T = self._dev(pb.T if T is None else T)
         assert rho_s.numel() == self.S * self.cells and ux.numel() == self.cells
         self._keep = (rho_s, ux, uy, T)
+        self._uses(*self._keep)
         dbm_set_state(self.h, rho_s.data_ptr(), ux.data_ptr(), uy.data_ptr(), T.data_ptr(), self._st())
 
     def set_f(self, f):
         f = self._dev(f)
         assert f.numel() == self.S * Q * self.cells
         self._keep = (f,)
+        self._uses(f)
         dbm_set_f(self.h, f.data_ptr(), self._st())
 
     def get_f(self):
         torch = self.torch
         out = torch.empty((self.S, Q, self.pb.ny, self.pb.nx), dtype=torch.float64, device=self.device)
         dbm_get_f(self.h, out.data_ptr(), self._st())
+        self._join()
         return out
 
     def step(self, nsteps: int = 1):
@@ -351,18 +372,21 @@ class Solver:
             out = torch.empty((4 * self.S + 5, self.pb.ny, self.pb.nx), dtype=torch.float64,
                               device=self.device)
         dbm_moments(self.h, out.data_ptr(), self._st())
+        self._join()
         return out
 
     def nonequilibrium(self):
         torch = self.torch
         out = torch.empty((20 * self.S, self.pb.ny, self.pb.nx), dtype=torch.float64, device=self.device)
         dbm_nonequilibrium(self.h, out.data_ptr(), self._st())
+        self._join()
         return out
 
     def conservation(self):
         torch = self.torch
         out = torch.empty(self.S + 4, dtype=torch.float64, device=self.device)
         dbm_conservation(self.h, out.data_ptr(), self._st())
+        self._join()
         return out
 
     def status(self):
@@ -441,12 +465,32 @@ class Batch:
         self.table = torch.empty(nb + 128, dtype=torch.uint8, device=dev)
         base = self.table.data_ptr()
         self._tp = (base + 127) // 128 * 128
+        self.table.record_stream(self.stream)
+        cur = torch.cuda.current_stream(dev)
+        self._others = []
+        for st in [cur] + [s.stream for s in self.solvers]:
+            if st is not None and st != self.stream and all(st != o for o in self._others):
+                self._others.append(st)
+        self._enter()
         self.b = dbm_batch_create(handles, self._tp, nb, self.stream.cuda_stream)
         if tune:
             dbm_batch_tune(self.b, self.stream.cuda_stream)
+        self._leave()
+
+    def _enter(self):
+        # the batch stream starts after the work queued on the caller's and
+        # the solvers' streams, which continue only after the batch's steps
+        for st in self._others:
+            self.stream.wait_stream(st)
+
+    def _leave(self):
+        for st in self._others:
+            st.wait_stream(self.stream)
 
     def step(self, nsteps: int):
+        self._enter()
         dbm_batch_step(self.b, nsteps, self.stream.cuda_stream)
+        self._leave()
 
     def info(self) -> dict:
         return dbm_batch_info(self.b)
