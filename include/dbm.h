@@ -227,10 +227,11 @@ int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes);
 int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t table_bytes, void *stream,
                      dbm_batch **out);
 
-/* Choose the tile shape (64x8, 32x8 or 32x16 cells) and the launch form
- * (as many CTAs as are resident at once, each walking a contiguous range
- * of tiles, or one CTA per tile) that step this batch fastest: each pair
- * is timed on `reps` trial launches that read the current states and write
+/* Choose the tile shape (64x8, 32x8, 32x16 or 32x12 cells), the launch form (as
+ * many CTAs as are resident at once, each walking a contiguous range of
+ * tiles, or one CTA per tile) and whether the tile copies promote L2 fills
+ * to 256 bytes, whichever step this batch fastest: each choice is timed on
+ * `reps` trial launches that read the current states and write
  * only the buffers the next step overwrites, so no state advances.
  * Synchronises the stream. */
 int dbm_batch_tune(dbm_batch *b, void *stream, int reps);

@@ -1,14 +1,20 @@
 // dbm_batch.cu -- many independent D2V16 problems stepped together.
 //
-// A batch groups bound FP32 handles with the same species count.  One
-// persistent kernel launch per time step walks the tiles of every instance
-// (instances may differ in grid size, boundaries, species constants,
-// reaction and time step): each CTA takes a contiguous range of tiles, looks
-// up each tile's instance in a table, copies that instance's step constants
-// into shared memory when the instance changes, stages the tile plus halo
-// with one TMA copy through the instance's own tensor map, and runs the
-// same per-cell arithmetic as the single-problem kernel.  Steps are replayed from captured CUDA graphs, and
-// the tile shape is chosen by timing each compiled shape (dbm_batch_tune).
+// A batch groups bound FP32 handles with the same species count.  Instances
+// may differ in grid size, boundaries, species constants, reaction and time
+// step.  The instances are split into chunks; per time step each chunk is
+// one kernel launch whose parameter block (the kernel's constant bank)
+// holds, for every instance of the chunk, its step constants, the TMA
+// descriptor of its input buffer and its output pointers.  A CTA takes one
+// tile (or a contiguous range of tiles) from the device tile list, stages
+// the tile plus halo with one TMA copy through its instance's descriptor
+// and runs the same per-cell arithmetic as the single-problem kernel, with
+// the constants read from the constant bank (shared-memory copies of them
+// would compete with the stencil reads).  Pairs of steps are replayed from
+// a CUDA graph in which each chunk is an independent two-launch chain; the
+// tile shape, launch form and L2 promotion are chosen by timing
+// (dbm_batch_tune).
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -19,73 +25,102 @@
 
 namespace dbm {
 
-// One instance as the batched kernel sees it (device table entry).
+// One instance of a launch: its input descriptor at the launch's parity,
+// step constants and outputs.
 template <int S>
-struct __align__(128) BatchEntry {
-    CUtensorMap tmap[2];  // input descriptor at parity 0 and parity 1
+struct __align__(64) BatchInst {
+    CUtensorMap tmap;
     StepConsts<float, S> c;
-    float *f[2];          // input buffer at parity 0 and parity 1
+    float *fout;
     unsigned *flag;
-    int tiles_x, tile_begin;
+};
+
+// Bytes a launch's parameter block may use (the kernel-parameter limit is
+// 32764 bytes; the tile-list pointer follows the block).
+constexpr int BATCH_PARAM_BYTES = 32 * 1024 - 256;
+
+// Parameter block of one launch: instances k0 .. k0+n-1 and their tiles
+// t0 .. t0+nt-1 of the device tile list.
+template <int S>
+struct BatchChunk {
+    static constexpr int CAP = (BATCH_PARAM_BYTES - 64) / (int)sizeof(BatchInst<S>);
+    int k0, n, t0, nt;
+    BatchInst<S> e[CAP];
+};
+static_assert(sizeof(BatchChunk<1>) <= BATCH_PARAM_BYTES && sizeof(BatchChunk<3>) <= BATCH_PARAM_BYTES,
+              "parameter block too large");
+
+// One tile of one instance, as a single 16-byte load.
+struct __align__(16) BatchTile {
+    int k;         // instance (index in the batch)
+    int bx0, by0;  // first interior cell of the tile
+    int pad;
 };
 
 template <int S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, 2)
-    k_step_batch(const BatchEntry<S> *__restrict__ tab, const int *__restrict__ tile_inst, int total, int parity)
+    k_step_batch(const __grid_constant__ BatchChunk<S> P, const BatchTile *__restrict__ tiles)
 {
     constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q;
     constexpr unsigned BYTES = (unsigned)(BX * BY * NP * sizeof(float));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
-    __shared__ StepConsts<float, S> sc;
     float *tile = reinterpret_cast<float *>(smem_raw);
-    const int tx = threadIdx.x, ty = threadIdx.y, nthr = TX * TY, tid = ty * TX + tx;
-    const bool leader = tid == 0;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool leader = tx == 0 && ty == 0;
     const unsigned b = smem_u32(&bar);
     if (leader) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    // a contiguous range of tiles per CTA: consecutive tiles mostly belong
-    // to the same instance, so its constants stay in shared memory
-    const int t0 = (int)((long long)total * blockIdx.x / gridDim.x);
-    const int t1 = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
-    int k_loaded = -1;
+    // one tile per CTA, or a contiguous range of tiles when the grid holds
+    // only the CTAs that are resident at once
+    const int t0 = P.t0 + (int)((long long)P.nt * blockIdx.x / gridDim.x);
+    const int t1 = P.t0 + (int)((long long)P.nt * (blockIdx.x + 1) / gridDim.x);
     unsigned phase = 0;
+    BatchTile next = tiles[t0];
     for (int t = t0; t < t1; ++t, phase ^= 1u) {
-        const int k = tile_inst[t];
-        const BatchEntry<S> &e = tab[k];
-        __syncthreads();  // the previous tile is done with the shared tile and constants
-        const int local = t - e.tile_begin;
-        const int bx0 = (local % e.tiles_x) * TX, by0 = (local / e.tiles_x) * TY;
-        if (leader) {
-            const unsigned long long tm = reinterpret_cast<unsigned long long>(&e.tmap[parity]);
-            // the descriptor lives in global memory: acquire it for the tensor-map proxy
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm) : "memory");
-            tma_tile_load(tile, tm, bx0, by0, b, BYTES);
-        }
-        if (k != k_loaded) {  // this instance's constants into shared memory
-            const unsigned *src = reinterpret_cast<const unsigned *>(&e.c);
-            unsigned *dst = reinterpret_cast<unsigned *>(&sc);
-            for (int j = tid; j < (int)(sizeof(sc) / 4); j += nthr) dst[j] = src[j];
-            k_loaded = k;
-            __syncthreads();
-        }
-        if (!mbar_wait(b, phase, TMA_WAIT_LIMIT)) {
+        const BatchTile cur = next;
+        if (t + 1 < t1) next = tiles[t + 1];
+        const BatchInst<S> &e = P.e[cur.k - P.k0];
+        __syncthreads();  // barrier initialised / previous tile no longer read
+        if (leader) tma_tile_load(tile, reinterpret_cast<unsigned long long>(&e.tmap), cur.bx0, cur.by0, b, BYTES);
+        const bool ok = mbar_wait(b, phase, TMA_WAIT_LIMIT);
+        if (__syncthreads_or(!ok)) {
+            // the copy did not land: report, give it one more bounded wait so
+            // that no copy is left writing into shared memory, leave together
             if (leader) raise_flag(e.flag, DBM_HEALTH_TIMEOUT);
             mbar_wait(b, phase, TMA_WAIT_LIMIT);
             return;
         }
-        const int x = bx0 + tx, y = by0 + ty;
-        if (x < sc.nx && y < sc.ny) {
+        const StepConsts<float, S> &c = e.c;
+        const int x = cur.bx0 + tx, y = cur.by0 + ty;
+        if (x < c.nx && y < c.ny) {
             SmemTile st;
             st.base = tile + (ty + 2) * BX + (tx + 4);
             st.P = BY * BX;
             st.py = BX;
-            StateOut o{e.f[parity ^ 1], sc.plane, sc.nx, sc.ny, sc.pitch};
-            step_cell<S>(sc, st, x, y, o, e.flag);
+            StateOutT<true> o{e.fout, c.plane, c.nx, c.ny, c.pitch};
+            step_cell<S>(c, st, x, y, o, e.flag);
         }
     }
+}
+
+// The compiled kernel of species count S and tile shape TX x TY.
+struct BatchKernel {
+    const void *fn;
+    int tx, ty;
+    size_t smem;
+    size_t chunk_bytes;
+    int cap;
+};
+
+template <int S, int TX, int TY>
+BatchKernel batch_kernel()
+{
+    return BatchKernel{(const void *)k_step_batch<S, TX, TY>, TX, TY,
+                       (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float), sizeof(BatchChunk<S>),
+                       BatchChunk<S>::CAP};
 }
 
 }  // namespace dbm
@@ -98,23 +133,43 @@ typedef CUresult (*encode_tiled_fn_b)(CUtensorMap *, CUtensorMapDataType, cuuint
                                       CUtensorMapFloatOOBfill);
 
 // Tile shapes compiled for the batched kernel.
-static const int N_SHAPES = 3;
-static const int SHAPE_TX[N_SHAPES] = {64, 32, 32};
-static const int SHAPE_TY[N_SHAPES] = {8, 8, 16};
+static const int N_SHAPES = 4;
+static const int SHAPE_TX[N_SHAPES] = {64, 32, 32, 32};
+static const int SHAPE_TY[N_SHAPES] = {8, 8, 16, 12};
+
+template <int S>
+static BatchKernel batch_kernel_s(int shape)
+{
+    switch (shape) {
+    case 0: return batch_kernel<S, 64, 8>();
+    case 1: return batch_kernel<S, 32, 8>();
+    case 2: return batch_kernel<S, 32, 16>();
+    default: return batch_kernel<S, 32, 12>();
+    }
+}
+
+static BatchKernel batch_kernel_for(int S, int shape)
+{
+    return S == 1 ? batch_kernel_s<1>(shape) : S == 2 ? batch_kernel_s<2>(shape) : batch_kernel_s<3>(shape);
+}
 
 struct dbm_batch {
     std::vector<dbm_handle *> h;
     int S;
-    int shape;                 // index into SHAPE_TX / SHAPE_TY
-    int persistent;            // 1: as many CTAs as fit at once; 0: one CTA per tile
-    int parity;                // steps taken mod 2
-    int total_tiles, ctas;
-    void *table;               // caller's device buffer
+    int shape;       // index into SHAPE_TX / SHAPE_TY
+    int persistent;  // 1: a launch has at most the CTAs resident at once; 0: one CTA per tile
+    int promote;     // 1: the tile copies promote L2 fills to 256 B; 0: no promotion
+    int parity;      // steps taken mod 2 since the parameter blocks were written
+    int total_tiles;
+    int resident;    // CTAs of the current kernel resident at once on the device
+    BatchKernel k;
+    void *table;  // caller's device buffer: the tile list
     size_t table_bytes;
-    unsigned char *host;       // staging copy of the table (128-byte aligned)
-    size_t host_bytes;
-    std::vector<long long> expected_steps;  // each handle's step count the table assumes
-    cudaGraphExec_t graph[2];         // two steps starting at parity 0 / 1
+    std::vector<BatchTile> tiles;  // host copy of the tile list
+    unsigned char *chunks;         // parameter blocks [chunk][parity], 64-byte aligned
+    int nchunks;
+    std::vector<long long> expected_steps;  // each handle's step count the blocks assume
+    cudaGraphExec_t graph[2];               // two steps starting at parity 0 / 1
     char err[512];
 };
 
@@ -122,12 +177,6 @@ static int bfail(dbm_batch *b, int code, const char *msg)
 {
     if (b) snprintf(b->err, sizeof(b->err), "%s", msg);
     return code;
-}
-
-template <int S>
-static size_t entry_bytes()
-{
-    return sizeof(BatchEntry<S>);
 }
 
 // Tiles per step of these handles with a TX x TY tile.
@@ -138,139 +187,188 @@ static long long count_tiles(dbm_handle *const *h, int n, int TX, int TY)
     return t;
 }
 
-// Table: n entries, then the instance of every tile (for the tile shape
-// with the most tiles).
+// Device table: the tile list for the tile shape with the most tiles.
 static size_t table_size(dbm_handle *const *h, int n)
 {
-    const int S = h[0]->p.nspecies;
-    const size_t e = S == 1 ? entry_bytes<1>() : S == 2 ? entry_bytes<2>() : entry_bytes<3>();
     long long most = 0;
     for (int sh = 0; sh < N_SHAPES; ++sh) {
         const long long t = count_tiles(h, n, SHAPE_TX[sh], SHAPE_TY[sh]);
         if (t > most) most = t;
     }
-    return e * n + (size_t)most * sizeof(int) + 256;
+    return (size_t)most * sizeof(BatchTile) + 256;
 }
 
+static unsigned char *chunk_block(dbm_batch *b, int j, int parity)
+{
+    return b->chunks + (size_t)(2 * j + parity) * b->k.chunk_bytes;
+}
+
+// Write the tile list (to the device, then synchronise the stream) and the
+// host parameter blocks of every chunk at both parities; parity 0 reads
+// each handle's current buffer.
 template <int S>
-static int write_table(dbm_batch *b, cudaStream_t st)
+static int write_tables(dbm_batch *b, cudaStream_t st)
 {
     const int n = (int)b->h.size();
-    const int TX = SHAPE_TX[b->shape], TY = SHAPE_TY[b->shape];
+    const int TX = b->k.tx, TY = b->k.ty;
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn)
         return bfail(b, DBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     encode_tiled_fn_b encode = (encode_tiled_fn_b)fn;
-    const size_t bytes = table_size(b->h.data(), n);
-    if (b->host_bytes < bytes) {
-        free(b->host);
-        b->host = (unsigned char *)aligned_alloc(128, (bytes + 127) / 128 * 128);
-        if (!b->host) return bfail(b, DBM_ERR_INVALID, "out of host memory");
-        b->host_bytes = bytes;
+    const int cap = BatchChunk<S>::CAP;
+    const int nchunks = (n + cap - 1) / cap;
+    const size_t bytes_all = (size_t)2 * nchunks * sizeof(BatchChunk<S>);
+    if (nchunks != b->nchunks || !b->chunks) {
+        free(b->chunks);
+        b->chunks = (unsigned char *)aligned_alloc(64, (bytes_all + 63) / 64 * 64);
+        b->nchunks = b->chunks ? nchunks : 0;
+        if (!b->chunks) return bfail(b, DBM_ERR_INVALID, "out of host memory");
     }
-    memset(b->host, 0, bytes);
+    memset(b->chunks, 0, bytes_all);
     b->expected_steps.assign(n, 0);
-    BatchEntry<S> *ent = reinterpret_cast<BatchEntry<S> *>(b->host);
-    int *tile_inst = reinterpret_cast<int *>(b->host + sizeof(BatchEntry<S>) * n);
-    int tiles = 0;
-    for (int k = 0; k < n; ++k) {
-        dbm_handle *h = b->h[k];
-        BatchEntry<S> &e = ent[k];
-        fill_step_consts<float, S>(h, e.c);
-        const int cur = h->cur;
-        b->expected_steps[k] = h->steps;
-        for (int par = 0; par < 2; ++par) {
-            void *in = h->f[cur ^ par];  // parity 0 reads the current state
-            e.f[par] = (float *)in;
-            const dbm_layout &L = h->lay;
-            cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)(16 * S)};
-            cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
-            cuuint32_t box[3] = {(cuuint32_t)(TX + 8), (cuuint32_t)(TY + 4), (cuuint32_t)(16 * S)};
-            cuuint32_t estr[3] = {1, 1, 1};
-            if (encode(&e.tmap[par], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, in, dims, strides, box, estr,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                return bfail(b, DBM_ERR_CUDA, "tensor map encoding failed");
+    b->tiles.clear();
+    for (int j = 0; j < nchunks; ++j) {
+        const int k0 = j * cap, k1 = k0 + cap < n ? k0 + cap : n;
+        const int t0 = (int)b->tiles.size();
+        BatchChunk<S> *blk[2] = {reinterpret_cast<BatchChunk<S> *>(chunk_block(b, j, 0)),
+                                 reinterpret_cast<BatchChunk<S> *>(chunk_block(b, j, 1))};
+        for (int k = k0; k < k1; ++k) {
+            dbm_handle *h = b->h[k];
+            b->expected_steps[k] = h->steps;
+            StepConsts<float, S> c;
+            fill_step_consts<float, S>(h, c);
+            const int tiles_x = (h->p.nx + TX - 1) / TX, nt = tiles_x * ((h->p.ny + TY - 1) / TY);
+            for (int u = 0; u < nt; ++u) b->tiles.push_back(BatchTile{k, (u % tiles_x) * TX, (u / tiles_x) * TY, 0});
+            for (int par = 0; par < 2; ++par) {
+                BatchInst<S> &e = blk[par]->e[k - k0];
+                void *in = h->f[h->cur ^ par];
+                const dbm_layout &L = h->lay;
+                cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)(16 * S)};
+                cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
+                cuuint32_t box[3] = {(cuuint32_t)(TX + 8), (cuuint32_t)(TY + 4), (cuuint32_t)(16 * S)};
+                cuuint32_t estr[3] = {1, 1, 1};
+                if (encode(&e.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, in, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           b->promote ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                    return bfail(b, DBM_ERR_CUDA, "tensor map encoding failed");
+                e.c = c;
+                e.fout = (float *)h->f[h->cur ^ par ^ 1];
+                e.flag = (unsigned *)h->scratch;
+            }
         }
-        e.flag = (unsigned *)h->scratch;
-        e.tiles_x = (h->p.nx + TX - 1) / TX;
-        e.tile_begin = tiles;
-        const int nt = e.tiles_x * ((h->p.ny + TY - 1) / TY);
-        for (int j = 0; j < nt; ++j) tile_inst[tiles + j] = k;
-        tiles += nt;
+        for (int par = 0; par < 2; ++par) {
+            blk[par]->k0 = k0;
+            blk[par]->n = k1 - k0;
+            blk[par]->t0 = t0;
+            blk[par]->nt = (int)b->tiles.size() - t0;
+        }
     }
-    b->total_tiles = tiles;
-    // the table is rewritten while its parity layout is "current input at parity 0"
-    cudaError_t er = cudaMemcpyAsync(b->table, b->host, bytes, cudaMemcpyHostToDevice, st);
+    b->total_tiles = (int)b->tiles.size();
+    const size_t bytes = b->tiles.size() * sizeof(BatchTile);
+    if (bytes > b->table_bytes) return bfail(b, DBM_ERR_INVALID, "tile list larger than the table");
+    cudaError_t er = cudaMemcpyAsync(b->table, b->tiles.data(), bytes, cudaMemcpyHostToDevice, st);
     if (er != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(er));
-    er = cudaStreamSynchronize(st);  // the staging buffer may change on the next write
+    er = cudaStreamSynchronize(st);  // the host list may change on the next write
     if (er != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(er));
     return DBM_OK;
 }
 
-static int grid_size(const dbm_batch *b)
+// Tiles of chunk j (the count sits in the block header: k0, n, t0, nt).
+static int chunk_tiles(const dbm_batch *b, int j)
 {
-    return b->persistent && b->ctas < b->total_tiles ? b->ctas : b->total_tiles;
+    return reinterpret_cast<const int *>(b->chunks + (size_t)(2 * j) * b->k.chunk_bytes)[3];
 }
 
-template <int S, int TX, int TY>
-static int launch_batch_t(dbm_batch *b, int parity, cudaStream_t st, bool set_attr)
+static int chunk_grid(const dbm_batch *b, int j)
 {
-    constexpr size_t smem = (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float);
-    if (set_attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_batch<S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    const int nt = chunk_tiles(b, j);
+    return b->persistent && b->resident < nt ? b->resident : nt;
+}
+
+// Launch arguments of chunk j at a parity (the block is copied at launch).
+struct ChunkArgs {
+    const BatchTile *tiles;
+    void *args[2];
+};
+
+static void chunk_args(dbm_batch *b, int j, int parity, ChunkArgs &a)
+{
+    a.tiles = (const BatchTile *)b->table;
+    a.args[0] = chunk_block(b, j, parity);
+    a.args[1] = &a.tiles;
+}
+
+// One time step of every chunk, launched in turn on the stream.
+static int launch_step_all(dbm_batch *b, int parity, cudaStream_t st)
+{
+    for (int j = 0; j < b->nchunks; ++j) {
+        ChunkArgs a;
+        chunk_args(b, j, parity, a);
+        cudaError_t e =
+            cudaLaunchKernel(b->k.fn, dim3(chunk_grid(b, j)), dim3(b->k.tx, b->k.ty), a.args, b->k.smem, st);
         if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_batch<S, TX, TY>, TX * TY, smem);
-        b->ctas = sms * (per > 0 ? per : 1);
-        return DBM_OK;
     }
-    const int n = (int)b->h.size();
-    const BatchEntry<S> *tab = reinterpret_cast<const BatchEntry<S> *>(b->table);
-    const int *tile_inst = reinterpret_cast<const int *>((const char *)b->table + sizeof(BatchEntry<S>) * n);
-    const int grid = grid_size(b);
-    k_step_batch<S, TX, TY><<<grid, dim3(TX, TY), smem, st>>>(tab, tile_inst, b->total_tiles, parity);
-    cudaError_t e = cudaGetLastError();
+    return DBM_OK;
+}
+
+// Two steps from `parity`: per chunk a chain of two kernel nodes; the
+// chunks' chains are independent of each other.
+static int build_graph(dbm_batch *b, int parity, cudaGraphExec_t *out)
+{
+    cudaGraph_t g;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
+    for (int j = 0; j < b->nchunks && e == cudaSuccess; ++j) {
+        cudaGraphNode_t prev = nullptr;
+        for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+            ChunkArgs a;
+            chunk_args(b, j, parity ^ s, a);
+            cudaKernelNodeParams kp;
+            memset(&kp, 0, sizeof(kp));
+            kp.func = const_cast<void *>(b->k.fn);
+            kp.gridDim = dim3(chunk_grid(b, j));
+            kp.blockDim = dim3(b->k.tx, b->k.ty);
+            kp.sharedMemBytes = (unsigned)b->k.smem;
+            kp.kernelParams = a.args;
+            cudaGraphNode_t node;
+            e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+            prev = node;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
     return e == cudaSuccess ? DBM_OK : bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
 }
 
-template <int S>
-static int launch_batch_s(dbm_batch *b, int parity, cudaStream_t st, bool set_attr)
-{
-    switch (b->shape) {
-    case 0: return launch_batch_t<S, 64, 8>(b, parity, st, set_attr);
-    case 1: return launch_batch_t<S, 32, 8>(b, parity, st, set_attr);
-    case 2: return launch_batch_t<S, 32, 16>(b, parity, st, set_attr);
-    }
-    return DBM_ERR_INVALID;
-}
-
-static int launch_batch(dbm_batch *b, int parity, cudaStream_t st, bool set_attr = false)
-{
-    switch (b->S) {
-    case 1: return launch_batch_s<1>(b, parity, st, set_attr);
-    case 2: return launch_batch_s<2>(b, parity, st, set_attr);
-    case 3: return launch_batch_s<3>(b, parity, st, set_attr);
-    }
-    return DBM_ERR_INVALID;
-}
-
-static int rebuild(dbm_batch *b, cudaStream_t st)
+static void drop_graphs(dbm_batch *b)
 {
     for (int g = 0; g < 2; ++g)
         if (b->graph[g]) {
             cudaGraphExecDestroy(b->graph[g]);
             b->graph[g] = nullptr;
         }
-    int rc = b->S == 1 ? write_table<1>(b, st) : b->S == 2 ? write_table<2>(b, st) : write_table<3>(b, st);
+}
+
+// Select the kernel of the current shape and rewrite every table for the
+// handles' current states.
+static int rebuild(dbm_batch *b, cudaStream_t st)
+{
+    drop_graphs(b);
+    b->k = batch_kernel_for(b->S, b->shape);
+    cudaError_t e = cudaFuncSetAttribute(b->k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->k.smem);
+    if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, b->k.fn, b->k.tx * b->k.ty, b->k.smem);
+    b->resident = sms * (per > 0 ? per : 1);
+    const int rc = b->S == 1 ? write_tables<1>(b, st) : b->S == 2 ? write_tables<2>(b, st) : write_tables<3>(b, st);
     if (rc) return rc;
-    b->parity = 0;  // the table now maps the current inputs to parity 0
-    return launch_batch(b, 0, st, true);
+    b->parity = 0;  // the blocks map each handle's current buffer to parity 0
+    return DBM_OK;
 }
 
 extern "C" {
@@ -299,18 +397,20 @@ int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t tabl
     }
     if (table_bytes < table_size(handles, n) || ((uintptr_t)table & 127)) return DBM_ERR_INVALID;
     dbm_batch *b = new dbm_batch();
-    b->host = nullptr;
-    b->host_bytes = 0;
     b->h.assign(handles, handles + n);
     b->S = S;
     b->shape = 0;
-    b->persistent = 1;
+    b->persistent = 0;
+    b->promote = 1;
     b->table = table;
     b->table_bytes = table_bytes;
+    b->chunks = nullptr;
+    b->nchunks = 0;
     b->graph[0] = b->graph[1] = nullptr;
+    b->err[0] = 0;
     const int rc = rebuild(b, (cudaStream_t)stream);
     if (rc) {
-        free(b->host);
+        free(b->chunks);
         delete b;
         return rc;
     }
@@ -335,41 +435,39 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
     cudaStream_t st = (cudaStream_t)stream;
     if (reps < 1) reps = 3;
     float best = 1e30f;
-    int best_shape = 0, best_mode = 1;
+    int best_shape = 0, best_mode = 0, best_promote = 1;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int trial = 0; trial < 2 * N_SHAPES; ++trial) {
-        const int sh = trial >> 1;
-        b->shape = sh;
+    int rc = DBM_OK;
+    for (int trial = 0; trial < 4 * N_SHAPES && !rc; ++trial) {
+        b->shape = trial >> 2;
         b->persistent = trial & 1;
-        int rc = rebuild(b, st);
-        // a trial launch reads the current states and writes the other
+        b->promote = (trial >> 1) & 1;
+        rc = rebuild(b, st);
+        // a trial step reads the current states and writes the other
         // buffers, which the next real step overwrites: no state advances
-        if (!rc) rc = launch_batch(b, 0, st);
-        if (!rc) {
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < reps && !rc; ++r) rc = launch_batch(b, 0, st);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-        }
+        if (!rc) rc = launch_step_all(b, 0, st);
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && !rc; ++r) rc = launch_step_all(b, 0, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (rc) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return rc;
-        }
-        if (ms < best) {
+        if (!rc && ms < best) {
             best = ms;
-            best_shape = sh;
+            best_shape = b->shape;
             best_mode = b->persistent;
+            best_promote = b->promote;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc) return rc;
     b->shape = best_shape;
     b->persistent = best_mode;
+    b->promote = best_promote;
     return rebuild(b, st);
 }
 
@@ -384,36 +482,27 @@ int dbm_batch_step(dbm_batch *b, int nsteps, void *stream)
             break;
         }
     int left = nsteps;
-    // graphs are captured on a created stream; on the legacy default stream
-    // the steps are launched one by one
+    // graphs run on a created stream; on the legacy default stream the
+    // steps are launched one by one
     const bool graphs = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     while (left >= 2 && !graphs) {
-        int rc = launch_batch(b, b->parity, st);
-        if (!rc) rc = launch_batch(b, b->parity ^ 1, st);
+        int rc = launch_step_all(b, b->parity, st);
+        if (!rc) rc = launch_step_all(b, b->parity ^ 1, st);
         if (rc) return rc;
         left -= 2;
     }
     while (left >= 2) {
         cudaGraphExec_t &g = b->graph[b->parity];
-        if (!g) {  // capture two steps starting at this parity
-            cudaGraph_t graph;
-            cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-            if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
-            int rc = launch_batch(b, b->parity, st);
-            if (!rc) rc = launch_batch(b, b->parity ^ 1, st);
-            e = cudaStreamEndCapture(st, &graph);
+        if (!g) {
+            const int rc = build_graph(b, b->parity, &g);
             if (rc) return rc;
-            if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
-            e = cudaGraphInstantiate(&g, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
         }
         cudaError_t e = cudaGraphLaunch(g, st);
         if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
         left -= 2;
     }
     if (left == 1) {
-        const int rc = launch_batch(b, b->parity, st);
+        const int rc = launch_step_all(b, b->parity, st);
         if (rc) return rc;
         b->parity ^= 1;
     }
@@ -427,7 +516,11 @@ int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int
     if (tile_x) *tile_x = SHAPE_TX[b->shape];
     if (tile_y) *tile_y = SHAPE_TY[b->shape];
     if (tiles) *tiles = b->total_tiles;
-    if (ctas) *ctas = grid_size(b);
+    if (ctas) {
+        int c = 0;
+        for (int j = 0; j < b->nchunks; ++j) c += chunk_grid(b, j);
+        *ctas = c;
+    }
     return DBM_OK;
 }
 
@@ -436,9 +529,8 @@ const char *dbm_batch_last_error(const dbm_batch *b) { return b ? b->err : "null
 void dbm_batch_destroy(dbm_batch *b)
 {
     if (!b) return;
-    for (int g = 0; g < 2; ++g)
-        if (b->graph[g]) cudaGraphExecDestroy(b->graph[g]);
-    free(b->host);
+    drop_graphs(b);
+    free(b->chunks);
     delete b;
 }
 

@@ -54,16 +54,16 @@ void fill_step_consts(const dbm_handle *h, StepConsts<real, S> &c)
         c.lam_l[s] = (real)(lam - (double)c.lam_h[s]);
         c.kap_h[s] = (real)kap;
         c.kap_l[s] = (real)(kap - (double)c.kap_h[s]);
-        c.tau_d[s] = sp.tau;
-        c.tau_a[s] = sp.tau * sp.a_stoich;
+        c.tau_d[s] = (real)sp.tau;
+        c.tau_a[s] = (real)(sp.tau * sp.a_stoich);
         src += (2.0 + sp.I) * sp.a_stoich;
     }
     c.accel_x = (real)p.accel[0];
     c.accel_y = (real)p.accel[1];
-    c.k_ov = p.k_ov;
-    c.Ea_over_R = p.Ea_over_R;
-    c.Qheat = p.Q;
-    c.src = src;
+    c.k_ov = (real)p.k_ov;
+    c.Ea_over_R = (real)p.Ea_over_R;
+    c.Qheat = (real)p.Q;
+    c.src = (real)src;
     c.fuel = p.fuel;
     c.oxid = p.oxidizer;
     c.has_reaction = p.k_ov != 0.0;

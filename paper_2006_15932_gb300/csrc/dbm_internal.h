@@ -50,8 +50,8 @@ struct StepConsts {
     real lam_h[S], lam_l[S], kap_h[S], kap_l[S];
     real dpi[S], inv_m[S], tau[S], dt_tau[S];
     real accel_x, accel_y;
-    double tau_d[S], tau_a[S];  // tau^s, tau^s a^s
-    double k_ov, Ea_over_R, Qheat, src;  // src = sum_s (D+I^s) a^s
+    real tau_d[S], tau_a[S];  // tau^s, tau^s a^s
+    real k_ov, Ea_over_R, Qheat, src;  // src = sum_s (D+I^s) a^s
     int fuel, oxid;
     int has_reaction, has_force;
     int nx, ny, pitch, bc_x, bc_y;

@@ -176,13 +176,11 @@ __device__ __forceinline__ void store_images(T *pl, int x, int y, int nx, int ny
 // cancelling subtraction in FP64 (W = sum lam E, w = sum lam n,
 // wd = sum kap n: the weights under which the update conserves momentum and
 // energy exactly).
-__device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux, float uy, double &Td)
+__device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux, float uy)
 {
     const float u2 = ux * ux + uy * uy;
     const double num = (double)W - (double)u2 * (double)w;
-    const float T = (float)num / wd;
-    Td = (double)T;
-    return T;
+    return (float)num / wd;
 }
 
 // Where the cell sits and which ghost images its values must also reach.
@@ -192,15 +190,24 @@ struct Site {
     long long cell;  // element offset of (x, y) in a plane
 };
 
-// Output of the FP32 state: f^{n+1}; ghost images of a species after all
-// 16 of its values are stored (the thread re-reads its own stores).
-struct StateOut {
+// Output of the FP32 state: f^{n+1}.  Ghost images either after all 16
+// values of a species are stored (the thread re-reads its own stores: no
+// registers held across the species loop, best where boundary cells are
+// rare) or as each value is stored (INLINE: no re-read latency, best for
+// small grids where most warps hold a boundary cell).
+template <bool INLINE>
+struct StateOutT {
+    static constexpr bool kInlineImages = INLINE;
     float *f;  // plane 0 of the output buffer
     long long P;
     int nx, ny, pitch;
     __device__ __forceinline__ void put(const Site &w, int p, float g, float) const
     {
         __stcs(f + (long long)p * P + w.cell, g);  // streamed: not re-read this step
+    }
+    __device__ __forceinline__ void image(const Site &w, int p, float g, float) const
+    {
+        store_images(f + (long long)p * P, w.x, w.y, nx, ny, pitch, w.mx, w.my, g);
     }
     __device__ __forceinline__ void put_n(const Site &, int, float) const {}
     __device__ __forceinline__ void put_mix(const Site &, float, float, float) const {}
@@ -213,6 +220,7 @@ struct StateOut {
     }
     __device__ __forceinline__ void images_mix(const Site &) const {}
 };
+using StateOut = StateOutT<false>;
 
 // The whole update of cell (x, y).
 template <int S, class K, class Tile, class Out>
@@ -257,8 +265,7 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
 
     // 2. mixture velocity and temperature
     const float ux = wx / w, uy = wy / w;
-    double Td;
-    const float T = mixture_T(we, w, wd, ux, uy, Td);
+    const float T = mixture_T(we, w, wd, ux, uy);
 
     unsigned bad = 0;
     float a = 0;  // sum_s |n^s|
@@ -271,11 +278,11 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
     if (!(T > 0.0f)) bad |= DBM_HEALTH_TEMPERATURE;
     if (!isfinite(T + ux + uy)) bad |= DBM_HEALTH_NONFINITE;
 
-    // 3. reaction: omega_ov and T' (state after a time tau^s), FP64
-    double om = 0.0, dT = 0.0;
+    // 3. reaction: omega_ov and T' (state after a time tau^s)
+    float om = 0.0f, dT = 0.0f;
     if (c.has_reaction) {
-        om = c.k_ov * (double)nf * (double)no * exp(-c.Ea_over_R / Td);
-        dT = (c.Qheat - 0.5 * Td * c.src) * om / (0.5 * (double)cap);
+        om = c.k_ov * nf * no * expf(-c.Ea_over_R / T);
+        dT = (c.Qheat - 0.5f * T * c.src) * om / (0.5f * cap);
     }
 
     Site w_;
@@ -303,10 +310,9 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
         {
             float nr = ns, Ts = T;
             if (c.has_reaction) {
-                const double e = (double)ns + c.tau_a[s] * om;
-                if (e < -1e-6 * (double)a) bad |= DBM_HEALTH_NSTAR;
-                nr = (float)e;
-                Ts = (float)(Td + c.tau_d[s] * dT);
+                nr = ns + c.tau_a[s] * om;
+                if (nr < -1e-6f * a) bad |= DBM_HEALTH_NSTAR;
+                Ts = T + c.tau_d[s] * dT;
             }
             fhat_blocks<float>(nr, ux, uy, Ts * c.inv_m[s], c.dpi[s], cb);
             if (c.has_force && ns != 0.0f) {  // an absent species feels no force
@@ -346,9 +352,15 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
                 d -= c.cdy[s][r] * nnd_diff_neg(t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1), t.ld(p, 0, 2));
             // 6. forward Euler: f + dt/tau (f^eq,tot - f) - dt v . grad f
             const float e = feq_of<float>(i, o);
-            out.put(w_, p, f0[i] + dtt * (e - f0[i]) - d, e);
+            const float g = f0[i] + dtt * (e - f0[i]) - d;
+            out.put(w_, p, g, e);
+            if constexpr (Out::kInlineImages) {
+                if (images) out.image(w_, p, g, e);
+            }
         }
-        if (images) out.images(w_, s);
+        if constexpr (!Out::kInlineImages) {
+            if (images) out.images(w_, s);
+        }
     }
     if (images) out.images_mix(w_);
     if (bad) raise_flag(flag, bad);

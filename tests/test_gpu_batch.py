@@ -62,7 +62,7 @@ def test_batch_tune_leaves_states_unchanged(D):
     before = [s.get_f().cpu().numpy() for s in sols]
     batch = D.Batch(sols, stream=stream, tune=True)
     info = batch.info()
-    assert info["tile"] in ((64, 8), (32, 8), (32, 16)) and info["tiles"] > 0
+    assert info["tile"] in ((64, 8), (32, 8), (32, 16), (32, 12)) and info["tiles"] > 0
     after = [s.get_f().cpu().numpy() for s in sols]
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
@@ -115,3 +115,53 @@ def test_batch_rejects_mixed_species_or_precision(D):
     for group in ([a, b], [a, c]):
         with pytest.raises(D.DbmError):
             D.Batch(group, stream=stream)
+
+
+@pytest.mark.parametrize("ns,n", [(1, 70), (2, 45), (3, 33)])
+def test_batch_spanning_several_launch_chunks(D, ns, n):
+    """More instances than one launch's parameter block holds (63, 39 and
+    28 instances for S = 1, 2, 3): the batch runs several chunks per step;
+    every instance must still match its own single-problem steps."""
+    rng = np.random.default_rng(40 + ns)
+    pbs = []
+    for k in range(n):
+        nx, ny = int(rng.integers(5, 41)), int(rng.integers(3, 29))
+        bc = (k % 2, (k // 2) % 2)
+        pbs.append(W.random_smooth(nx, ny, ns, seed=100 * ns + k, reactive=(ns == 3 and k % 2 == 0),
+                                   force=(k % 4 == 1), bc=bc))
+    stream = torch.cuda.Stream()
+    solo, mixed = [], []
+    for pb in pbs:
+        for group in (solo, mixed):
+            s = D.Solver(pb, "fp32", stream=stream)
+            s.set_state()
+            group.append(s)
+    for s in solo:
+        s.step(7)
+    batch = D.Batch(mixed, stream=stream, tune=(ns == 2))
+    batch.step(7)  # three graph pairs and one single step
+    torch.cuda.synchronize()
+    # same per-cell arithmetic, compiled into different kernels (the
+    # compiler may contract different products); the force term's
+    # difference of two equilibria amplifies those last-bit differences
+    for a, b in zip(solo, mixed):
+        assert b.status()[0] == 0
+        assert rel(b.get_f().cpu().numpy(), a.get_f().cpu().numpy()) <= 4e-6
+
+
+def test_batch_on_the_default_stream(D):
+    """Without a created stream the steps are launched one by one."""
+    pbs = _mixed(5, seed=21)
+    solo, mixed = [], []
+    for pb in pbs:
+        for group in (solo, mixed):
+            s = D.Solver(pb, "fp32")
+            s.set_state()
+            group.append(s)
+    for s in solo:
+        s.step(6)
+    batch = D.Batch(mixed, stream=torch.cuda.default_stream(), tune=False)
+    batch.step(6)
+    torch.cuda.synchronize()
+    for a, b in zip(solo, mixed):
+        assert rel(b.get_f().cpu().numpy(), a.get_f().cpu().numpy()) <= 1e-6
