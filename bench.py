@@ -40,11 +40,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="kh4096", choices=["kh4096", "reactive", "sod", "batched"])
+    ap.add_argument("--workload", default="kh4096", choices=["kh4096", "reactive", "sod", "batched", "serve"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and e2e side legs")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--grid", default=None, help="override the grid, e.g. 2048x1024 (profiling runs)")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-steps", default="1000,10000", help="step counts drawn uniformly in lo,hi")
+    ap.add_argument("--serve-sides", default="128,2048", help="sides drawn log-uniformly in lo,hi")
+    ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / measured capacity")
+    ap.add_argument("--serve-qmax", type=int, default=128)
     return ap.parse_args()
 
 
@@ -56,13 +61,16 @@ def make_workload(name, grid=None):
         return W.kh_shear_layer(nx or 4096, ny=ny)
     if name == "reactive":
         return W.reactive_premixed(nx or 1024, ny or 256)
+    if name in ("batched", "serve"):  # the oracle's sample: one mid-size instance of the mix
+        return W.shock_instance(nx or 288, W.SEED)
     return W.sod_tube(nx or 400, 2000)
 
 
 def workload_config(pb, name, precision):
     return {
         "workload": {"kh4096": "kelvin_helmholtz_shear_layer", "reactive": "reactive_premixed_2d",
-                     "sod": "sod_shock_tube"}[name],
+                     "sod": "sod_shock_tube", "batched": "batched_shock_and_reactive_instances",
+                     "serve": "serve_poisson_request_mix"}[name],
         "grid": [pb.nx, pb.ny],
         "species": pb.ns,
         "velocities": 16,
@@ -245,6 +253,100 @@ def run_reference(args):
     return 0
 
 
+def run_serve(args, D, dev):
+    """Serving: Poisson arrivals of the request mix at a fraction of the
+    measured capacity, continuous batching; p50/p99 latency and throughput,
+    against first-come-first-served sequential solves (FP64 and unbatched
+    FP32) whose service times come from throughputs measured here."""
+    import torch
+
+    from paper_2006_15932_gb300 import serve as SV
+    from paper_2006_15932_gb300 import workloads as W
+
+    s_lo, s_hi = (int(v) for v in args.serve_sides.split(","))
+    n_lo, n_hi = (int(v) for v in args.serve_steps.split(","))
+    specs = W.serving_requests(args.serve_requests, lo=s_lo, hi=s_hi, steps=(n_lo, n_hi))
+    # capacity: the same mix (other seed, 1/20 of the steps) all arriving at once
+    cal = W.serving_requests(32, seed=W.SEED + 1, lo=s_lo, hi=s_hi,
+                             steps=(max(1, n_lo // 20), max(2, n_hi // 20)))
+    SV.Server(device=dev, qmax=args.serve_qmax).run(cal[:4])  # warm-up: kernels, allocator
+    cap = SV.summarize(SV.Server(device=dev, qmax=args.serve_qmax).run(cal))["throughput"]
+    mean_units = sum(s.units for s in specs) / len(specs)
+    rate = args.serve_load * cap / mean_units
+    specs = W.poisson_arrivals(specs, rate)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    srv = SV.Server(device=dev, qmax=args.serve_qmax)
+    res = srv.run(specs)
+    clk = clocks.stop()
+    if any(r.status for r in res):
+        raise SystemExit("health flag raised while serving")
+    summ = SV.summarize(res)
+
+    # sequential references: FP64 and unbatched FP32 throughput per species
+    # count on a 512 x 512 shock tube (FP64 is ALU-bound, so its rate hardly
+    # depends on the size)
+    def rate_of(precision, ns, steps):
+        spec = W.RequestSpec(rid=0, kind="shock", L=512, ns=ns, seed=1, nsteps=steps)
+        st = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(st):
+            s = D.Solver(W.request_problem(spec), precision, device=dev)
+            s.set_state(*W.request_fields(spec, dev))
+            s.step(2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            s.step(steps)
+            e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.close()
+        return 512 * 512 * ns * steps / (ms * 1e-3)
+
+    nss = sorted({s.ns for s in specs})
+    r64 = {ns: rate_of("fp64", ns, 4) for ns in nss}
+    r32 = {ns: rate_of("fp32", ns, 200) for ns in nss}
+    seq64 = SV.simulate_sequential(specs, r64)
+    seq32 = SV.simulate_sequential(specs, r32)
+    peak, peak_kind = measured_peaks()
+    bpu = BYTES_PER_UPDATE["fp32"]
+    cfg = {"workload": "serve_poisson_request_mix", "requests": len(specs), "sides": [s_lo, s_hi],
+           "side_distribution": "log-uniform", "species": nss, "reactive_fraction": 0.5,
+           "steps": [n_lo, n_hi], "precision": "fp32", "arrival_rate_per_s": rate,
+           "load": args.serve_load, "capacity_units_per_s": cap, "qmax": args.serve_qmax,
+           "batch_config": {k: (list(v) if isinstance(v, tuple) else v) for k, v in srv.config.items()},
+           "l2_policy": "inputs larger than L2"}
+    line = {"metric": METRIC, "value": summ["throughput"], "unit": UNIT, "n_gpus": 1, "steps": len(specs),
+            "warmup": 4, "ms_per_step": 1e3 * summ["makespan_s"] / len(specs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded request mix, Poisson arrivals)", "config": cfg,
+            "serve": {"p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "mean_s": summ["mean_s"],
+                      "makespan_s": summ["makespan_s"], "units": summ["units"],
+                      "hbm_budget_bytes": srv.adm.budget, "admitted_peak_bytes": srv.adm.peak,
+                      "batch_rebuilds": sum(g.rebuilds for g in srv.groups.values()),
+                      "quanta": srv.launch_quanta,
+                      "hbm_frac_whole_run": summ["throughput"] * bpu / 1e9 / peak},
+            "fp64_sequential": dict(seq64, rate_by_species=r64,
+                                    how="FIFO one request at a time; service = units / FP64 rate measured "
+                                        "on a 512x512 tube per species count"),
+            "fp32_unbatched_sequential": dict(seq32, rate_by_species=r32,
+                                              how="FIFO one request at a time; service = units / single-"
+                                                  "problem FP32 rate measured on a 512x512 tube"),
+            "clocks": clk, "e2e": {"value": summ["throughput"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                   "d2h_bytes_per_step": 8 * (max(nss) + 4)},
+            "roofline": {"bound": "hbm", "achieved": summ["throughput"] * bpu / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": summ["throughput"] * bpu / 1e9 / peak, "traffic": None,
+                         "kernel": "all step kernels of the run (whole-run average)",
+                         "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -263,6 +365,10 @@ def main():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "serve":
+        B.build()
+        D.load()
+        return run_serve(args, D, dev) if rank == 0 else 0
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -242,6 +242,18 @@ int dbm_batch_step(dbm_batch *b, int nsteps, void *stream);
 /* Current tile shape, number of tiles per step and CTAs per launch. */
 int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int *ctas);
 
+/* The batch's kernel configuration: tile shape, launch form (1: at most
+ * the CTAs resident at once, each over a contiguous range of tiles; 0: one
+ * CTA per tile) and L2 promotion of the tile copies (1: 256 B; 0: none). */
+int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote);
+
+/* Set the configuration (a compiled tile shape: 64x8, 32x8, 32x16 or
+ * 32x12), rewriting the batch's tables; synchronises the stream.  The tile
+ * shape selects the compiled kernel, so two batches with the same shape
+ * give bitwise the same result for the same instance, whatever else they
+ * hold.  DBM_ERR_INVALID for a shape that is not compiled. */
+int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, void *stream);
+
 const char *dbm_batch_last_error(const dbm_batch *b);
 void dbm_batch_destroy(dbm_batch *b);
 

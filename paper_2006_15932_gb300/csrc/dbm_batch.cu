@@ -524,6 +524,29 @@ int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int
     return DBM_OK;
 }
 
+int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote)
+{
+    if (!b) return DBM_ERR_INVALID;
+    if (tile_x) *tile_x = SHAPE_TX[b->shape];
+    if (tile_y) *tile_y = SHAPE_TY[b->shape];
+    if (persistent) *persistent = b->persistent;
+    if (promote) *promote = b->promote;
+    return DBM_OK;
+}
+
+int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, void *stream)
+{
+    if (!b || (persistent != 0 && persistent != 1) || (promote != 0 && promote != 1)) return DBM_ERR_INVALID;
+    int shape = -1;
+    for (int sh = 0; sh < N_SHAPES; ++sh)
+        if (SHAPE_TX[sh] == tile_x && SHAPE_TY[sh] == tile_y) shape = sh;
+    if (shape < 0) return bfail(b, DBM_ERR_INVALID, "tile shape not compiled for batches");
+    b->shape = shape;
+    b->persistent = persistent;
+    b->promote = promote;
+    return rebuild(b, (cudaStream_t)stream);
+}
+
 const char *dbm_batch_last_error(const dbm_batch *b) { return b ? b->err : "null batch"; }
 
 void dbm_batch_destroy(dbm_batch *b)

@@ -40,7 +40,8 @@ EXPORTS = [
     "dbm_bind", "dbm_set_state", "dbm_set_f", "dbm_get_f", "dbm_step", "dbm_moments",
     "dbm_nonequilibrium", "dbm_conservation", "dbm_conservation_noalloc", "dbm_status", "dbm_steps_taken",
     "dbm_last_error", "dbm_destroy", "dbm_batch_table_bytes", "dbm_batch_create", "dbm_batch_tune",
-    "dbm_batch_step", "dbm_batch_info", "dbm_batch_last_error", "dbm_batch_destroy",
+    "dbm_batch_step", "dbm_batch_info", "dbm_batch_get_config", "dbm_batch_set_config", "dbm_batch_last_error",
+    "dbm_batch_destroy",
 ]
 
 
@@ -137,6 +138,8 @@ def load(path: str = LIB_PATH):
     L.dbm_batch_tune.argtypes = [vp, vp, C.c_int]
     L.dbm_batch_step.argtypes = [vp, C.c_int, vp]
     L.dbm_batch_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
+    L.dbm_batch_get_config.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
+    L.dbm_batch_set_config.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     L.dbm_batch_last_error.argtypes = [vp]
     L.dbm_batch_last_error.restype = C.c_char_p
     L.dbm_batch_destroy.argtypes = [vp]
@@ -445,15 +448,27 @@ def dbm_batch_info(b) -> dict:
     return {"tile": (v[0].value, v[1].value), "tiles": v[2].value, "ctas": v[3].value}
 
 
+def dbm_batch_get_config(b) -> dict:
+    v = [C.c_int() for _ in range(4)]
+    _bcheck(b, load().dbm_batch_get_config(b, *[C.byref(x) for x in v]))
+    return {"tile": (v[0].value, v[1].value), "persistent": v[2].value, "promote": v[3].value}
+
+
+def dbm_batch_set_config(b, tile, persistent: int, promote: int, stream: int = 0) -> None:
+    _bcheck(b, load().dbm_batch_set_config(b, int(tile[0]), int(tile[1]), int(persistent), int(promote), stream))
+
+
 def dbm_batch_destroy(b) -> None:
     load().dbm_batch_destroy(b)
 
 
 class Batch:
-    """Solvers (FP32, same species count) stepped together by one persistent
-    launch per step, replayed from CUDA graphs on the solvers' stream."""
+    """Solvers (FP32, same species count) stepped together: one launch per
+    step and chunk of instances, pairs of steps replayed from a CUDA graph.
+    The kernel configuration is tuned (``tune``), given (``config``, a dict
+    as returned by ``config()``), or the library's default."""
 
-    def __init__(self, solvers, stream=None, tune=True):
+    def __init__(self, solvers, stream=None, tune=True, config=None):
         import torch
 
         self.torch = torch
@@ -473,7 +488,10 @@ class Batch:
                 self._others.append(st)
         self._enter()
         self.b = dbm_batch_create(handles, self._tp, nb, self.stream.cuda_stream)
-        if tune:
+        if config is not None:
+            dbm_batch_set_config(self.b, config["tile"], config["persistent"], config["promote"],
+                                 self.stream.cuda_stream)
+        elif tune:
             dbm_batch_tune(self.b, self.stream.cuda_stream)
         self._leave()
 
@@ -494,6 +512,9 @@ class Batch:
 
     def info(self) -> dict:
         return dbm_batch_info(self.b)
+
+    def config(self) -> dict:
+        return dbm_batch_get_config(self.b)
 
     def close(self):
         if self.b:

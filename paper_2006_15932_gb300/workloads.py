@@ -267,3 +267,124 @@ def batched_instances(n: int = 64, seed: int = SEED, lo: int = 64, hi: int = 512
         pb.nsteps = int(rng.integers(1000, 2001))
         out.append(pb)
     return out
+
+
+# ---------------------------------------------------------------------------
+# serving: requests arriving over time
+# ---------------------------------------------------------------------------
+
+@dataclass
+class RequestSpec:
+    """One serving request: an L x L instance of ``ns`` species, a shock
+    tube or a reactive gas, advanced by ``nsteps`` steps; ``arrival`` in
+    seconds after the start of the run."""
+    rid: int
+    kind: str
+    L: int
+    ns: int
+    seed: int
+    nsteps: int
+    arrival: float = 0.0
+
+    @property
+    def units(self) -> int:  # species-cell updates the request asks for
+        return self.L * self.L * self.ns * self.nsteps
+
+    @property
+    def cells(self) -> int:
+        return self.L * self.L
+
+
+def serving_requests(n: int = 200, seed: int = SEED, lo: int = 128, hi: int = 2048, steps=(1000, 10000),
+                     species_counts=(2, 3, 4), reactive_frac: float = 0.5) -> List[RequestSpec]:
+    """The serving mix: sides log-uniform in [lo, hi], species count uniform
+    over ``species_counts``, a fraction ``reactive_frac`` reactive gases (the
+    rest shock tubes), step counts uniform in ``steps`` (inclusive).
+    Arrival times are left at 0 (the caller draws them)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        L = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        ns = int(rng.choice(species_counts))
+        kind = "reactive" if rng.uniform() < reactive_frac else "shock"
+        nsteps = int(rng.integers(steps[0], steps[1] + 1))
+        out.append(RequestSpec(rid=k, kind=kind, L=L, ns=ns, seed=int(rng.integers(0, 2**31)), nsteps=nsteps))
+    return out
+
+
+def poisson_arrivals(specs: List[RequestSpec], rate: float, seed: int = SEED) -> List[RequestSpec]:
+    """Copies of ``specs`` with Poisson arrivals at ``rate`` per second
+    (exponential gaps, the first request at its gap after t = 0)."""
+    rng = np.random.default_rng(seed + 1)
+    t = 0.0
+    out = []
+    for s in specs:
+        t += float(rng.exponential(1.0 / rate)) if rate > 0 else 0.0
+        out.append(replace(s, arrival=t))
+    return out
+
+
+def _stoich(ns: int):
+    """Fuel, oxidiser and stoichiometric coefficients of the one-step
+    reaction of an ns-species request (equal masses, so sum a m = 0)."""
+    if ns == 1:
+        return 0, 0, [0.0]
+    if ns == 2:
+        return 0, 0, [-1.0, 1.0]  # F -> P, rate k n_F n_F exp(-E_a/T)
+    if ns == 3:
+        return 0, 1, [-1.0, -1.0, 2.0]
+    a = [-1.0, -1.0] + [2.0 / (ns - 2)] * (ns - 2)
+    return 0, 1, a
+
+
+def request_problem(spec: RequestSpec) -> Problem:
+    """The problem of a request without its initial fields (those come from
+    ``request_fields``, on any device)."""
+    rng = np.random.default_rng(spec.seed)
+    L, ns = spec.L, spec.ns
+    if spec.kind == "reactive":
+        fuel, oxid, a = _stoich(ns)
+        sp = [species(tau=2e-5, a=a[s]) for s in range(ns)]
+        return Problem(name=f"req{spec.rid}_reactive_{L}_s{ns}", nx=L, ny=L, species=sp, dx=1e-3, dy=1e-3,
+                       dt=1e-5, bc_x=PERIODIC, bc_y=PERIODIC, fuel=fuel, oxid=oxid,
+                       k_ov=float(rng.uniform(20.0, 40.0)), Ea_over_R=float(rng.uniform(2.0, 3.0)),
+                       Q=float(rng.uniform(0.3, 0.6)), nsteps=spec.nsteps)
+    sp = [species(tau=2e-5) for _ in range(ns)]
+    return Problem(name=f"req{spec.rid}_shock_{L}_s{ns}", nx=L, ny=L, species=sp, dx=1e-3, dy=1e-3, dt=1e-5,
+                   bc_x=OUTFLOW, bc_y=PERIODIC, nsteps=spec.nsteps)
+
+
+def request_fields(spec: RequestSpec, device="cpu"):
+    """Initial fields (rho_s (S, L, L), ux, uy, T) of a request as FP64 torch
+    tensors on ``device``: a Sod-type tube along x with a seeded transverse
+    perturbation of the interface (shock), or a premixed gas with a hot
+    product spot at the centre (reactive)."""
+    import torch
+
+    rng = np.random.default_rng(spec.seed + 7)
+    L, ns = spec.L, spec.ns
+    f64 = dict(dtype=torch.float64, device=device)
+    y = torch.arange(L, **f64)[:, None].expand(L, L)
+    x = torch.arange(L, **f64)[None, :].expand(L, L)
+    zero = torch.zeros((L, L), **f64)
+    if spec.kind == "reactive":
+        fuel, oxid, a = _stoich(ns)
+        r2 = ((x - L / 2) ** 2 + (y - L / 2) ** 2) / (L / 8) ** 2
+        hot = torch.exp(-r2)
+        reac = 0.95 - 0.9 * hot  # reactant mass fraction
+        reactants = [s for s in range(ns) if a[s] < 0]
+        products = [s for s in range(ns) if a[s] > 0]
+        rho_s = torch.empty((ns, L, L), **f64)
+        for s in range(ns):
+            if s in reactants:
+                rho_s[s] = reac / len(reactants)
+            else:
+                rho_s[s] = (1.0 - reac) / len(products)
+        return rho_s, zero, zero.clone(), 1.0 + 0.8 * hot
+    ph = float(rng.uniform(0, 2 * math.pi))
+    x0 = L / 2 + 2.0 * torch.sin(2 * math.pi * y / L + ph)
+    left = x < x0
+    rho = torch.where(left, 1.0, 0.125).to(**f64)
+    p = torch.where(left, 1.0, 0.1).to(**f64)
+    rho_s = (rho / ns).unsqueeze(0).repeat(ns, 1, 1)
+    return rho_s, zero, zero.clone(), p / rho

@@ -1,0 +1,93 @@
+"""Serving (continuous batching) on the GPU: results do not depend on the
+mix a request is served in, admission respects the HBM budget, and every
+request gets exactly its own number of steps."""
+import numpy as np
+import pytest
+
+from paper_2006_15932_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_15932_gb300 import build as B
+    from paper_2006_15932_gb300 import dbm, serve
+
+    B.build()
+    dbm.load()
+    return serve
+
+
+def _mix():
+    rng = np.random.default_rng(7)
+    specs = []
+    for k in range(9):
+        specs.append(W.RequestSpec(rid=k, kind="reactive" if k % 2 else "shock", L=int(rng.integers(30, 90)),
+                                   ns=(2, 3, 4)[k % 3], seed=1000 + k, nsteps=int(rng.integers(9, 40)),
+                                   arrival=0.01 * k))
+    return specs
+
+
+def _alone(S, spec):
+    srv = S.Server(qmax=8, keep_f=True, hbm_budget=1 << 32)
+    spec0 = W.RequestSpec(**{**spec.__dict__, "arrival": 0.0})
+    (r,) = srv.run([spec0])
+    return r
+
+
+def test_same_result_alone_and_in_the_mix(S):
+    from paper_2006_15932_gb300 import dbm as D
+
+    specs = _mix()
+    srv = S.Server(qmax=8, keep_f=True, hbm_budget=1 << 32)
+    res = {r.rid: r for r in srv.run(specs)}
+    assert sorted(res) == [s.rid for s in specs]
+    assert all(r.status == 0 for r in res.values())
+    # several quanta, several rebuilds: the mix really changed under the requests
+    assert sum(g.rebuilds for g in srv.groups.values()) >= 3
+    for spec in specs:
+        alone = _alone(S, spec)
+        np.testing.assert_array_equal(alone.f, res[spec.rid].f)
+        np.testing.assert_array_equal(alone.conservation, res[spec.rid].conservation)
+    # and the served result is the plain FP32 solve of the same problem
+    for spec in specs[:3]:
+        s = D.Solver(W.request_problem(spec), "fp32")
+        s.set_state(*W.request_fields(spec, "cuda"))
+        s.step(spec.nsteps)
+        f = s.get_f().cpu().numpy()
+        assert np.max(np.abs(f - res[spec.rid].f)) / np.max(np.abs(f)) <= 4e-6
+
+
+def test_admission_respects_the_hbm_budget(S):
+    specs = [W.RequestSpec(rid=k, kind="shock", L=64, ns=2, seed=k, nsteps=20, arrival=0.0) for k in range(6)]
+    one = S.footprint(W.request_problem(specs[0]))
+    srv = S.Server(qmax=4, hbm_budget=int(2.5 * one))
+    res = srv.run(specs)
+    assert len(res) == 6 and all(r.status == 0 for r in res)
+    assert srv.adm.peak <= srv.adm.budget and srv.adm.peak == 2 * one
+    assert srv.adm.used == 0
+    # first come, first served: admission times follow the request order
+    adm = [r.admitted for r in sorted(res, key=lambda r: r.rid)]
+    assert adm == sorted(adm)
+
+
+def test_request_larger_than_the_budget_is_refused(S):
+    spec = W.RequestSpec(rid=0, kind="shock", L=64, ns=2, seed=0, nsteps=3)
+    srv = S.Server(hbm_budget=1000)
+    with pytest.raises(ValueError):
+        srv.run([spec])
+
+
+def test_zero_step_request_returns_its_initial_state(S):
+    from paper_2006_15932_gb300 import dbm as D
+
+    spec = W.RequestSpec(rid=0, kind="reactive", L=40, ns=3, seed=3, nsteps=0)
+    srv = S.Server(keep_f=True, hbm_budget=1 << 32)
+    (r,) = srv.run([spec])
+    s = D.Solver(W.request_problem(spec), "fp32")
+    s.set_state(*W.request_fields(spec, "cuda"))
+    np.testing.assert_array_equal(r.f, s.get_f().cpu().numpy())
