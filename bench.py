@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="kh4096", choices=["kh4096", "reactive", "sod", "batched", "serve"])
+    ap.add_argument("--workload", default="kh4096", choices=["kh4096", "reactive", "sod", "batched", "serve",
+                                                                    "precision_kh", "precision_reactive"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and e2e side legs")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -50,6 +51,8 @@ def parse():
     ap.add_argument("--serve-sides", default="128,2048", help="sides drawn log-uniformly in lo,hi")
     ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / measured capacity")
     ap.add_argument("--serve-qmax", type=int, default=128)
+    ap.add_argument("--study-steps", type=int, default=None,
+                    help="steps of a precision study (1000 for precision_kh, 20000 for precision_reactive)")
     return ap.parse_args()
 
 
@@ -117,7 +120,8 @@ def step_kernel_name(pb, precision):
     if precision == "bf16dev":
         return f"k_step_bf16<{pb.ns},64,8>"
     if pb.ns <= 3:
-        return f"k_step_tma<float,{pb.ns},{64 if pb.ns <= 2 else 32},8>"
+        tx, ty = {1: (64, 8), 2: (32, 16), 3: (32, 8)}[pb.ns]
+        return f"k_step_tma<float,{pb.ns},{tx},{ty}>"
     return f"k_step<float,{pb.ns}>"
 
 
@@ -347,6 +351,102 @@ def run_serve(args, D, dev):
     return 0
 
 
+def run_precision(args, D, dev):
+    """Precision study: the same initial state advanced in FP64, FP32 and
+    BF16DEV (the latter only where its scope allows), relative L2 and
+    L-infinity errors of the mixture fields against FP64 at checkpoints, and
+    each precision's drift of the conserved totals over the run."""
+    import torch
+
+    from paper_2006_15932_gb300 import workloads as W
+
+    if args.workload == "precision_kh":
+        nx, ny = (int(v) for v in (args.grid or "4096x4096").lower().split("x"))
+        pb = W.kh_shear_layer(nx, ny=ny)
+        total = args.study_steps or 1000
+        precs = ["fp64", "fp32", "bf16dev"]
+        checkpoints = 4
+    else:
+        nx, ny = (int(v) for v in (args.grid or "1024x256").lower().split("x"))
+        pb = W.reactive_premixed(nx, ny)
+        total = args.study_steps or 20000
+        precs = ["fp64", "fp32"]
+        checkpoints = 10
+    st = torch.cuda.Stream(device=dev)
+    sols = {}
+    with torch.cuda.stream(st):
+        for p in precs:
+            sols[p] = D.Solver(pb, p, device=dev)
+            sols[p].set_state()
+        cons0 = {p: sols[p].conservation().cpu().numpy() for p in precs}
+    S = pb.ns
+    names = ["rho", "ux", "uy", "T"]
+    rows = {"rho": 4 * S, "ux": 4 * S + 1, "uy": 4 * S + 2, "T": 4 * S + 3}
+    # velocity errors are measured against the velocity scale of the run
+    # (max |u| of the FP64 field, at least the sound speed 1), not against a
+    # field that may vanish
+    curve = []
+    per = total // checkpoints
+    done = 0
+    t_fp64 = 0.0
+    while done < total:
+        n = min(per, total - done)
+        with torch.cuda.stream(st):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            sols["fp64"].step(n)
+            e1.record(st)
+            for p in precs[1:]:
+                sols[p].step(n)
+            mom = {p: sols[p].moments() for p in precs}
+        st.synchronize()
+        t_fp64 += e0.elapsed_time(e1) * 1e-3
+        done += n
+        ref = mom["fp64"]
+        entry = {"step": done}
+        for p in precs[1:]:
+            errs = {}
+            for nm in names:
+                a, b = mom[p][rows[nm]], ref[rows[nm]]
+                scale = torch.max(torch.abs(b))
+                if nm in ("ux", "uy"):
+                    scale = torch.maximum(torch.max(torch.abs(ref[rows["ux"]]).max(), torch.abs(ref[rows["uy"]]).max()),
+                                          torch.tensor(1.0, dtype=torch.float64, device=dev))
+                d = a - b
+                errs[nm] = {"rel_linf": float(torch.max(torch.abs(d)) / scale),
+                            "rel_l2": float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(b)
+                                            if nm not in ("ux", "uy") else
+                                            torch.linalg.vector_norm(d) / (scale * math.sqrt(d.numel())))}
+            entry[p] = errs
+        curve.append(entry)
+        del mom, ref
+    drift = {}
+    with torch.cuda.stream(st):
+        for p in precs:
+            c1 = sols[p].conservation().cpu().numpy()
+            c0 = cons0[p]
+            mass0 = float(sum(abs(c0[:S])))
+            e_scale = abs(float(c0[S + 2])) + abs(float(c0[S + 3]))
+            drift[p] = {"mass": float(abs(sum(c1[:S]) - sum(c0[:S])) / mass0),
+                        "momentum_x": float(abs(c1[S] - c0[S]) / mass0),
+                        "momentum_y": float(abs(c1[S + 1] - c0[S + 1]) / mass0),
+                        "energy_plus_bound_heat": float(abs((c1[S + 2] + c1[S + 3]) - (c0[S + 2] + c0[S + 3]))
+                                                        / e_scale)}
+    for p in precs:
+        rc, bits = sols[p].status()
+        if rc != 0:
+            raise SystemExit(f"health flag raised in {p}: bits={bits}")
+        sols[p].close()
+    line = {"study": args.workload, "grid": [pb.nx, pb.ny], "species": S, "steps": total,
+            "boundary": ["periodic" if b == 0 else "outflow" for b in (pb.bc_x, pb.bc_y)],
+            "reactive": pb.k_ov != 0.0, "fp64_seconds": t_fp64,
+            "error_vs_fp64": curve, "conservation_drift": drift,
+            "norms": "rel_linf = max|a-b| / max|b|, rel_l2 = ||a-b|| / ||b||; for u_x, u_y the scale is "
+                     "max(max|u|, 1) (and rms of that scale for L2)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -369,6 +469,10 @@ def main():
         B.build()
         D.load()
         return run_serve(args, D, dev) if rank == 0 else 0
+    if args.workload.startswith("precision"):
+        B.build()
+        D.load()
+        return run_precision(args, D, dev) if rank == 0 else 0
     dist = None
     if world > 1:
         import torch.distributed as dist

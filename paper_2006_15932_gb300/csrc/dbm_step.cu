@@ -13,16 +13,12 @@ int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st);
 template <int S, int TX, int TY>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, void *fout, cudaStream_t st);
 
-// Tile shapes of the TMA-staged kernel (FP32, one cell per thread): 64 x 8
-// cells for one or two species (110.6 KB of shared memory for two, two
-// CTAs of 512 threads per SM), 32 x 8 for three.
 bool tma_supported(const dbm_params &p) { return p.precision == DBM_FP32 && p.nspecies <= 3; }
 
 static int tma_box(const dbm_params &p, unsigned box[3])
 {
-    const int tx = p.nspecies <= 2 ? 64 : 32, ty = 8;
-    box[0] = tx + 8;
-    box[1] = ty + 4;
+    box[0] = tma_tile_x(p.nspecies) + 8;
+    box[1] = tma_tile_y(p.nspecies) + 4;
     box[2] = 16 * p.nspecies;
     return 0;
 }
@@ -86,9 +82,9 @@ int launch_step(dbm_handle *h, int cur, cudaStream_t st)
     if (h->tma_ok && want != DBM_KERNEL_GENERIC) {
         const CUtensorMap *tm = &h->tmap[cur];
         switch (h->p.nspecies) {
-        case 1: return launch_step_tma_t<1, 64, 8>(h, tm, fout, st);
-        case 2: return launch_step_tma_t<2, 64, 8>(h, tm, fout, st);
-        case 3: return launch_step_tma_t<3, 32, 8>(h, tm, fout, st);
+        case 1: return launch_step_tma_t<1, tma_tile_x(1), tma_tile_y(1)>(h, tm, fout, st);
+        case 2: return launch_step_tma_t<2, tma_tile_x(2), tma_tile_y(2)>(h, tm, fout, st);
+        case 3: return launch_step_tma_t<3, tma_tile_x(3), tma_tile_y(3)>(h, tm, fout, st);
         }
     }
     if (want == DBM_KERNEL_TMA) return DBM_ERR_INVALID;

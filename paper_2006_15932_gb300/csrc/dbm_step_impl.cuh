@@ -172,15 +172,22 @@ __device__ __forceinline__ void store_images(T *pl, int x, int y, int nx, int ny
     }
 }
 
-// Mixture temperature T = (W - (u.u) w) / wd of one cell, with the
-// cancelling subtraction in FP64 (W = sum lam E, w = sum lam n,
-// wd = sum kap n: the weights under which the update conserves momentum and
-// energy exactly).
+// Mixture temperature T = (W - (u.u) w) / wd of one cell (W = sum lam E,
+// w = sum lam n, wd = sum kap n: the weights under which the update
+// conserves momentum and energy exactly).  The cancelling subtraction is
+// carried in float-float: the product (u.u) w = p + pe exactly (FMA) and
+// W - p = s + se exactly (Knuth's two-sum), so the numerator is as accurate
+// as an FP64 evaluation while every operation stays on the FP32 pipes.  The
+// _rn intrinsics keep the compiler from contracting these steps.
 __device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux, float uy)
 {
     const float u2 = ux * ux + uy * uy;
-    const double num = (double)W - (double)u2 * (double)w;
-    return (float)num / wd;
+    const float p = __fmul_rn(u2, w);
+    const float pe = fmaf(u2, w, -p);
+    const float s = __fsub_rn(W, p);
+    const float bb = __fsub_rn(s, W);
+    const float se = __fadd_rn(__fsub_rn(W, __fsub_rn(s, bb)), __fsub_rn(-p, bb));
+    return __fadd_rn(s, __fsub_rn(se, pe)) / wd;
 }
 
 // Where the cell sits and which ghost images its values must also reach.
@@ -264,7 +271,8 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
     }
 
     // 2. mixture velocity and temperature
-    const float ux = wx / w, uy = wy / w;
+    const float rw = 1.0f / w;
+    const float ux = wx * rw, uy = wy * rw;
     const float T = mixture_T(we, w, wd, ux, uy);
 
     unsigned bad = 0;
