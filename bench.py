@@ -120,7 +120,7 @@ def step_kernel_name(pb, precision):
     if precision == "bf16dev":
         return f"k_step_bf16<{pb.ns},64,8>"
     if pb.ns <= 3:
-        tx, ty = {1: (64, 8), 2: (32, 16), 3: (32, 8)}[pb.ns]
+        tx, ty = {1: (32, 16), 2: (32, 16), 3: (32, 8)}[pb.ns]
         return f"k_step_tma<float,{pb.ns},{tx},{ty}>"
     return f"k_step<float,{pb.ns}>"
 
@@ -139,6 +139,22 @@ def ncu_traffic(name, precision):
     if not e or e.get("source_sha") != kernel_source_sha():
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def combine_ranks(ms_local, updates_per_rank, dist=None, device=None):
+    """Whole-job throughput of replicas: every rank advanced its own
+    independent problem by updates_per_rank species-cell updates; the job
+    took as long as the slowest rank.  Returns (max ms over ranks, total
+    updates of all ranks / that time)."""
+    import torch
+
+    ms = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None and dist.is_initialized():
+        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms_max = float(ms.item())
+    return ms_max, updates_per_rank * world / (ms_max * 1e-3)
 
 
 class ClockSampler:
@@ -555,12 +571,8 @@ def main():
         rc, bits = s_.status()
         if rc != 0:
             raise SystemExit(f"health flag raised during the benchmark: rc={rc} bits={bits}")
-    ms = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(ms, op=dist.ReduceOp.MAX)
-    ms_max = float(ms.item())
     updates_per_rank = units * K
-    value = updates_per_rank * world / (ms_max * 1e-3)
+    ms_max, value = combine_ranks(ms_total, updates_per_rank, dist, dev)
 
     peak, peak_kind = measured_peaks()
     bpu = bytes_per_update(args.precision, pb.ns)

@@ -93,11 +93,13 @@ struct dbm_handle {
 namespace dbm {
 
 // Tile of the TMA-staged FP32 step (one cell per thread), by species count:
-// 64 x 8 cells for one species, 32 x 16 for two (102 KB of shared memory,
-// two CTAs of 512 threads per SM; measured fastest of 64x8, 32x12, 32x16,
-// 64x6, 32x8 and 64x4 on the 4096^2 shear layer), 32 x 8 for three.
-constexpr int tma_tile_x(int S) { return S == 1 ? 64 : 32; }
-constexpr int tma_tile_y(int S) { return S == 2 ? 16 : 8; }
+// 32 x 16 cells for one or two species (102 KB of shared memory for two,
+// two CTAs of 512 threads per SM), 32 x 8 for three (92 KB, 256 threads).
+// Measured fastest among 64x8, 32x16, 32x12, 64x16, 32x8, 64x12, 128x4,
+// 64x6, 64x4, 32x6 and 32x4 on 4096 x 4096 (two species), 4096 x 2048 (one)
+// and 2048 x 2048 (three) grids.
+constexpr int tma_tile_x(int S) { return 32; }
+constexpr int tma_tile_y(int S) { return S <= 2 ? 16 : 8; }
 
 // Launchers; each returns DBM_OK or DBM_ERR_CUDA (message in h->err).
 int launch_step(dbm_handle *h, int cur, cudaStream_t st);
