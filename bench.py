@@ -107,7 +107,8 @@ def measured_peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for rel in ("paper_2006_15932_gb300/csrc/dbm_step_impl.cuh", "paper_2006_15932_gb300/csrc/dbm_device.cuh"):
+    for rel in ("paper_2006_15932_gb300/csrc/dbm_step_impl.cuh", "paper_2006_15932_gb300/csrc/dbm_device.cuh",
+                "paper_2006_15932_gb300/csrc/dbm_internal.h", "paper_2006_15932_gb300/csrc/dbm_step.cu"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
