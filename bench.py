@@ -520,6 +520,7 @@ def main():
         cfg["tile"] = list(info["tile"])
         cfg["ctas_per_launch"] = info["ctas"]
         cfg["tiles_per_step"] = info["tiles"]
+        cfg["batch_config"] = {k: (list(v) if isinstance(v, tuple) else v) for k, v in batch.config().items()}
         units = sum(q.nx * q.ny * q.ns for q in pbs)
         per_call = 2  # one graph replay = two steps
 

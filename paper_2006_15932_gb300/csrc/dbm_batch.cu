@@ -12,8 +12,8 @@
 // the constants read from the constant bank (shared-memory copies of them
 // would compete with the stencil reads).  Pairs of steps are replayed from
 // a CUDA graph in which each chunk is an independent two-launch chain; the
-// tile shape, launch form and L2 promotion are chosen by timing
-// (dbm_batch_tune).
+// tile shape, launch form, L2 promotion and ghost-image policy are chosen by
+// timing (dbm_batch_tune).
 #include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -28,7 +28,7 @@ namespace dbm {
 // One instance of a launch: its input descriptor at the launch's parity,
 // step constants and outputs.
 template <int S>
-struct __align__(64) BatchInst {
+struct __align__(128) BatchInst {  // CUtensorMap is 128-byte aligned
     CUtensorMap tmap;
     StepConsts<float, S> c;
     float *fout;
@@ -43,7 +43,7 @@ constexpr int BATCH_PARAM_BYTES = 32 * 1024 - 256;
 // t0 .. t0+nt-1 of the device tile list.
 template <int S>
 struct BatchChunk {
-    static constexpr int CAP = (BATCH_PARAM_BYTES - 64) / (int)sizeof(BatchInst<S>);
+    static constexpr int CAP = (BATCH_PARAM_BYTES - 128) / (int)sizeof(BatchInst<S>);
     int k0, n, t0, nt;
     BatchInst<S> e[CAP];
 };
@@ -57,7 +57,7 @@ struct __align__(16) BatchTile {
     int pad;
 };
 
-template <int S, int TX, int TY>
+template <int S, int TX, int TY, bool INLINE_IMAGES>
 __global__ void __launch_bounds__(TX *TY, 2)
     k_step_batch(const __grid_constant__ BatchChunk<S> P, const BatchTile *__restrict__ tiles)
 {
@@ -100,13 +100,16 @@ __global__ void __launch_bounds__(TX *TY, 2)
             st.base = tile + (ty + 2) * BX + (tx + 4);
             st.P = BY * BX;
             st.py = BX;
-            StateOutT<true> o{e.fout, c.plane, c.nx, c.ny, c.pitch};
+            StateOutT<INLINE_IMAGES> o{e.fout, c.plane, c.nx, c.ny, c.pitch};
             step_cell<S>(c, st, x, y, o, e.flag);
         }
     }
 }
 
-// The compiled kernel of species count S and tile shape TX x TY.
+// The compiled kernel of species count S, tile shape TX x TY and ghost-image
+// policy (inline: each value's images stored with it, best when most warps
+// hold a boundary cell; otherwise after each species from the thread's own
+// stores).
 struct BatchKernel {
     const void *fn;
     int tx, ty;
@@ -116,10 +119,11 @@ struct BatchKernel {
 };
 
 template <int S, int TX, int TY>
-BatchKernel batch_kernel()
+BatchKernel batch_kernel(bool inline_images)
 {
-    return BatchKernel{(const void *)k_step_batch<S, TX, TY>, TX, TY,
-                       (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float), sizeof(BatchChunk<S>),
+    const void *fn = inline_images ? (const void *)k_step_batch<S, TX, TY, true>
+                                   : (const void *)k_step_batch<S, TX, TY, false>;
+    return BatchKernel{fn, TX, TY, (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float), sizeof(BatchChunk<S>),
                        BatchChunk<S>::CAP};
 }
 
@@ -138,19 +142,20 @@ static const int SHAPE_TX[N_SHAPES] = {64, 32, 32, 32};
 static const int SHAPE_TY[N_SHAPES] = {8, 8, 16, 12};
 
 template <int S>
-static BatchKernel batch_kernel_s(int shape)
+static BatchKernel batch_kernel_s(int shape, bool inl)
 {
     switch (shape) {
-    case 0: return batch_kernel<S, 64, 8>();
-    case 1: return batch_kernel<S, 32, 8>();
-    case 2: return batch_kernel<S, 32, 16>();
-    default: return batch_kernel<S, 32, 12>();
+    case 0: return batch_kernel<S, 64, 8>(inl);
+    case 1: return batch_kernel<S, 32, 8>(inl);
+    case 2: return batch_kernel<S, 32, 16>(inl);
+    default: return batch_kernel<S, 32, 12>(inl);
     }
 }
 
-static BatchKernel batch_kernel_for(int S, int shape)
+static BatchKernel batch_kernel_for(int S, int shape, bool inl)
 {
-    return S == 1 ? batch_kernel_s<1>(shape) : S == 2 ? batch_kernel_s<2>(shape) : batch_kernel_s<3>(shape);
+    return S == 1 ? batch_kernel_s<1>(shape, inl) : S == 2 ? batch_kernel_s<2>(shape, inl)
+                                                           : batch_kernel_s<3>(shape, inl);
 }
 
 struct dbm_batch {
@@ -159,6 +164,7 @@ struct dbm_batch {
     int shape;       // index into SHAPE_TX / SHAPE_TY
     int persistent;  // 1: a launch has at most the CTAs resident at once; 0: one CTA per tile
     int promote;     // 1: the tile copies promote L2 fills to 256 B; 0: no promotion
+    int inline_images;  // 1: ghost images stored with each value; 0: after each species
     int parity;      // steps taken mod 2 since the parameter blocks were written
     int total_tiles;
     int resident;    // CTAs of the current kernel resident at once on the device
@@ -166,7 +172,7 @@ struct dbm_batch {
     void *table;  // caller's device buffer: the tile list
     size_t table_bytes;
     std::vector<BatchTile> tiles;  // host copy of the tile list
-    unsigned char *chunks;         // parameter blocks [chunk][parity], 64-byte aligned
+    unsigned char *chunks;         // parameter blocks [chunk][parity], 128-byte aligned
     int nchunks;
     std::vector<long long> expected_steps;  // each handle's step count the blocks assume
     cudaGraphExec_t graph[2];               // two steps starting at parity 0 / 1
@@ -222,7 +228,7 @@ static int write_tables(dbm_batch *b, cudaStream_t st)
     const size_t bytes_all = (size_t)2 * nchunks * sizeof(BatchChunk<S>);
     if (nchunks != b->nchunks || !b->chunks) {
         free(b->chunks);
-        b->chunks = (unsigned char *)aligned_alloc(64, (bytes_all + 63) / 64 * 64);
+        b->chunks = (unsigned char *)aligned_alloc(128, (bytes_all + 127) / 128 * 128);
         b->nchunks = b->chunks ? nchunks : 0;
         if (!b->chunks) return bfail(b, DBM_ERR_INVALID, "out of host memory");
     }
@@ -357,7 +363,7 @@ static void drop_graphs(dbm_batch *b)
 static int rebuild(dbm_batch *b, cudaStream_t st)
 {
     drop_graphs(b);
-    b->k = batch_kernel_for(b->S, b->shape);
+    b->k = batch_kernel_for(b->S, b->shape, b->inline_images != 0);
     cudaError_t e = cudaFuncSetAttribute(b->k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->k.smem);
     if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
     int dev = 0, sms = 0, per = 0;
@@ -402,6 +408,7 @@ int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t tabl
     b->shape = 0;
     b->persistent = 0;
     b->promote = 1;
+    b->inline_images = 1;
     b->table = table;
     b->table_bytes = table_bytes;
     b->chunks = nullptr;
@@ -435,15 +442,16 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
     cudaStream_t st = (cudaStream_t)stream;
     if (reps < 1) reps = 3;
     float best = 1e30f;
-    int best_shape = 0, best_mode = 0, best_promote = 1;
+    int best_shape = 0, best_mode = 0, best_promote = 1, best_inline = 1;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = DBM_OK;
-    for (int trial = 0; trial < 4 * N_SHAPES && !rc; ++trial) {
-        b->shape = trial >> 2;
+    for (int trial = 0; trial < 8 * N_SHAPES && !rc; ++trial) {
+        b->shape = trial >> 3;
         b->persistent = trial & 1;
         b->promote = (trial >> 1) & 1;
+        b->inline_images = (trial >> 2) & 1;
         rc = rebuild(b, st);
         // a trial step reads the current states and writes the other
         // buffers, which the next real step overwrites: no state advances
@@ -460,6 +468,7 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
             best_shape = b->shape;
             best_mode = b->persistent;
             best_promote = b->promote;
+            best_inline = b->inline_images;
         }
     }
     cudaEventDestroy(e0);
@@ -468,6 +477,7 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
     b->shape = best_shape;
     b->persistent = best_mode;
     b->promote = best_promote;
+    b->inline_images = best_inline;
     return rebuild(b, st);
 }
 
@@ -524,19 +534,24 @@ int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int
     return DBM_OK;
 }
 
-int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote)
+int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote,
+                         int *inline_images)
 {
     if (!b) return DBM_ERR_INVALID;
     if (tile_x) *tile_x = SHAPE_TX[b->shape];
     if (tile_y) *tile_y = SHAPE_TY[b->shape];
     if (persistent) *persistent = b->persistent;
     if (promote) *promote = b->promote;
+    if (inline_images) *inline_images = b->inline_images;
     return DBM_OK;
 }
 
-int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, void *stream)
+int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, int inline_images,
+                         void *stream)
 {
-    if (!b || (persistent != 0 && persistent != 1) || (promote != 0 && promote != 1)) return DBM_ERR_INVALID;
+    if (!b || (persistent != 0 && persistent != 1) || (promote != 0 && promote != 1) ||
+        (inline_images != 0 && inline_images != 1))
+        return DBM_ERR_INVALID;
     int shape = -1;
     for (int sh = 0; sh < N_SHAPES; ++sh)
         if (SHAPE_TX[sh] == tile_x && SHAPE_TY[sh] == tile_y) shape = sh;
@@ -544,6 +559,7 @@ int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, i
     b->shape = shape;
     b->persistent = persistent;
     b->promote = promote;
+    b->inline_images = inline_images;
     return rebuild(b, (cudaStream_t)stream);
 }
 

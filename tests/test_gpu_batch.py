@@ -119,7 +119,7 @@ def test_batch_rejects_mixed_species_or_precision(D):
 
 @pytest.mark.parametrize("ns,n", [(1, 70), (2, 45), (3, 33)])
 def test_batch_spanning_several_launch_chunks(D, ns, n):
-    """More instances than one launch's parameter block holds (63, 39 and
+    """More instances than one launch's parameter block holds (63, 36 and
     28 instances for S = 1, 2, 3): the batch runs several chunks per step;
     every instance must still match its own single-problem steps."""
     rng = np.random.default_rng(40 + ns)
