@@ -388,3 +388,28 @@ def request_fields(spec: RequestSpec, device="cpu"):
     p = torch.where(left, 1.0, 0.1).to(**f64)
     rho_s = (rho / ns).unsqueeze(0).repeat(ns, 1, 1)
     return rho_s, zero, zero.clone(), p / rho
+
+
+def air_shock(nx: int = 600, nsteps: int = 12000) -> Problem:
+    """The air shock of section "Shock wave" (Eq. ConfigurationShock):
+    79 % N2 / 21 % O2 by mole (diatomic, I = 3), pre-shock air at rest
+    (1.17092 kg/m^3, 300 K) to the right of x0 = nx/4, the printed post-shock
+    state (1.58407 kg/m^3, 106.637 m/s, 333.612 K) to the left.  Units: the
+    pre-shock density and temperature, the molar mass of air (0.02885 kg/mol,
+    so that the mean particle mass is 1) and the speed sqrt(R T / M_air) =
+    294.04 m/s; then m_N2 = 0.97100, m_O2 = 1.10914.  Outflow in x, one row."""
+    Rg, M_air = 8.314462618, 0.02885
+    c_ref = math.sqrt(Rg * 300.0 / M_air)
+    mN2, mO2 = 0.0280134 / M_air, 0.0319988 / M_air
+    yN2 = 0.79 * mN2  # mass fractions (mean particle mass 1)
+    yO2 = 0.21 * mO2
+    rho_l, u_l, T_l = 1.58407 / 1.17092, 106.637 / c_ref, 333.612 / 300.0
+    x = np.arange(nx)[None, :]
+    left = x < nx // 4
+    rho = np.where(left, rho_l, 1.0)
+    ux = np.where(left, u_l, 0.0)
+    T = np.where(left, T_l, 1.0)
+    sp = [species(m=mN2, I=3.0, tau=2e-5), species(m=mO2, I=3.0, tau=2e-5)]
+    return Problem(name=f"air_shock_{nx}", nx=nx, ny=1, species=sp, dx=1e-3, dy=1e-3, dt=1e-5, bc_x=OUTFLOW,
+                   bc_y=PERIODIC, nsteps=nsteps, rho_s=np.stack([yN2 * rho, yO2 * rho]).astype(np.float64),
+                   ux=ux.astype(np.float64), uy=np.zeros((1, nx)), T=T.astype(np.float64))
