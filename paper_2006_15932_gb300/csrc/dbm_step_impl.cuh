@@ -305,9 +305,11 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
     const bool images = (w_.mx | w_.my) != 0u;
     out.put_mix(w_, ux, uy, T);
 
-    // the species loop is unrolled up to four species: the constants of each
-    // species then index the constant bank directly (measured 6-8 % faster)
-#pragma unroll(S <= 4 ? S : 1)
+    // the species loop is unrolled up to three species: the constants of each
+    // species then index the constant bank directly (measured 6-8 % faster
+    // for one to three species; the four-species generic kernel ran 30 %
+    // slower unrolled)
+#pragma unroll(S <= 3 ? S : 1)
     for (int s = 0; s < S; ++s) {
         float f0[Q];
 #pragma unroll

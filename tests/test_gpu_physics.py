@@ -83,7 +83,9 @@ def test_air_shock_rankine_hugoniot_and_nonequilibrium(D, precision):
         assert peak > 0
         assert d2[w].min() > -1e-3 * peak
         assert abs(int(np.argmax(d2[w])) + w.start - front) <= 4
-        assert np.max(np.abs(d2[pl])) < 1e-4 * peak
+        # (FP32: Delta_2 is a difference of two moments of order one, so
+        # the stored values' rounding leaves noise of ~1e-6 on the plateau)
+        assert np.max(np.abs(d2[pl])) < (1e-4 if precision == "fp64" else 1e-3) * peak
         # M_2xx(f^eq)/2 = (n^s T + rho^s u_x^2)/2: the exact counterpart of the figure
         n_s = m[4 * sp]
         ref = 0.5 * (n_s * T + n_s * pb.species[sp].m * ux ** 2)
