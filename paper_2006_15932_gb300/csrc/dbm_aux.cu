@@ -36,6 +36,33 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// FP32 storage: f = f^eq(rho^s / m^s, u, T) through the symmetry blocks in
+// FP64 (40 multiply-adds per species instead of the 256 of the full M^-1;
+// the blocks reproduce M^-1 to 1e-13, far below the rounding to float).
+template <int S>
+__global__ void __launch_bounds__(256)
+    k_set_state_blocks(const __grid_constant__ StepConsts<double, S> c, float *__restrict__ f,
+                       const double *__restrict__ rho_s, const double *__restrict__ ux,
+                       const double *__restrict__ uy, const double *__restrict__ T)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= c.nx || y >= c.ny) return;
+    const long long N = (long long)c.nx * c.ny;
+    const long long d = (long long)y * c.nx + x;
+    const long long cell = (long long)(y + GY) * c.pitch + (x + GX);
+    const Images im = cell_images(x, y, c.nx, c.ny, c.bc_x, c.bc_y);
+    const double u_x = ux[d], u_y = uy[d], t = T[d];
+#pragma unroll 1
+    for (int s = 0; s < S; ++s) {
+        double cb[16], o[16];
+        fhat_blocks<double>(rho_s[s * N + d] * c.inv_m[s], u_x, u_y, t * c.inv_m[s], c.dpi[s], cb);
+        solve_blocks<double>(c, s, cb, o);
+        for (int i = 0; i < Q; ++i)
+            store_with_images(f + (s * Q + i) * c.plane, cell, x, y, c.pitch, im, (float)feq_of<double>(i, o));
+    }
+}
+
 template <typename real>
 __global__ void __launch_bounds__(256)
     k_set_f(real *__restrict__ f, const double *__restrict__ src, int nplanes, int nx, int ny,
@@ -318,9 +345,15 @@ template <typename real, int S>
 static void set_state_t(dbm_handle *h, void *f, const double *rho_s, const double *ux,
                         const double *uy, const double *T, cudaStream_t st)
 {
+    dim3 b(32, 8);
+    if (sizeof(real) == 4) {
+        StepConsts<double, S> c;
+        fill_step_consts<double, S>(h, c);
+        k_set_state_blocks<S><<<cell_grid(h, b), b, 0, st>>>(c, (float *)f, rho_s, ux, uy, T);
+        return;
+    }
     OutConsts<S> c;
     fill_out_consts<S>(h, c);
-    dim3 b(32, 8);
     k_set_state<real, S><<<cell_grid(h, b), b, 0, st>>>(c, (real *)f, rho_s, ux, uy, T);
 }
 
