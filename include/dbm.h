@@ -227,7 +227,7 @@ int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes);
 int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t table_bytes, void *stream,
                      dbm_batch **out);
 
-/* Choose the tile shape (64x8, 32x8, 32x16 or 32x12 cells), the launch form (as
+/* Choose the tile shape (32x10, 32x8, 32x16 or 32x12 cells), the launch form (as
  * many CTAs as are resident at once, each walking a contiguous range of
  * tiles, or one CTA per tile), whether the tile copies promote L2 fills to
  * 256 bytes and whether ghost images are stored with each value or after
@@ -251,7 +251,7 @@ int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int
 int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote,
                          int *inline_images);
 
-/* Set the configuration (a compiled tile shape: 64x8, 32x8, 32x16 or
+/* Set the configuration (a compiled tile shape: 32x10, 32x8, 32x16 or
  * 32x12), rewriting the batch's tables; synchronises the stream.  The tile
  * shape selects the compiled kernel, so two batches with the same shape
  * give bitwise the same result for the same instance, whatever else they

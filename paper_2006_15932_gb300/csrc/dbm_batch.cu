@@ -58,7 +58,7 @@ struct __align__(16) BatchTile {
 };
 
 template <int S, int TX, int TY, bool INLINE_IMAGES>
-__global__ void __launch_bounds__(TX *TY, 2)
+__global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
     k_step_batch(const __grid_constant__ BatchChunk<S> P, const BatchTile *__restrict__ tiles)
 {
     constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q;
@@ -138,14 +138,14 @@ typedef CUresult (*encode_tiled_fn_b)(CUtensorMap *, CUtensorMapDataType, cuuint
 
 // Tile shapes compiled for the batched kernel.
 static const int N_SHAPES = 4;
-static const int SHAPE_TX[N_SHAPES] = {64, 32, 32, 32};
-static const int SHAPE_TY[N_SHAPES] = {8, 8, 16, 12};
+static const int SHAPE_TX[N_SHAPES] = {32, 32, 32, 32};
+static const int SHAPE_TY[N_SHAPES] = {10, 8, 16, 12};
 
 template <int S>
 static BatchKernel batch_kernel_s(int shape, bool inl)
 {
     switch (shape) {
-    case 0: return batch_kernel<S, 64, 8>(inl);
+    case 0: return batch_kernel<S, 32, 10>(inl);
     case 1: return batch_kernel<S, 32, 8>(inl);
     case 2: return batch_kernel<S, 32, 16>(inl);
     default: return batch_kernel<S, 32, 12>(inl);

@@ -93,13 +93,26 @@ struct dbm_handle {
 namespace dbm {
 
 // Tile of the TMA-staged FP32 step (one cell per thread), by species count:
-// 32 x 16 cells for one or two species (102 KB of shared memory for two,
-// two CTAs of 512 threads per SM), 32 x 8 for three (92 KB, 256 threads).
-// Measured fastest among 64x8, 32x16, 32x12, 64x16, 32x8, 64x12, 128x4,
-// 64x6, 64x4, 32x6 and 32x4 on 4096 x 4096 (two species), 4096 x 2048 (one)
-// and 2048 x 2048 (three) grids.
+// 32 x 8 cells for one species (31 KB of shared memory, four CTAs of 256
+// threads per SM), 32 x 10 for two (72 KB, three CTAs of 320 threads), 32 x 8
+// for three (92 KB, two CTAs).  Measured fastest among 64x8, 32x16, 32x12,
+// 32x10, 32x9, 32x7, 40x8, 48x6, 64x6, 64x5, 64x4, 32x20, 128x4 and others
+// on 4096 x 4096 (two species), 4096 x 2048 (one) and 2048 x 2048 (three)
+// grids: more resident CTAs per SM hide each CTA's wait for its tile.
 constexpr int tma_tile_x(int S) { return 32; }
-constexpr int tma_tile_y(int S) { return S <= 2 ? 16 : 8; }
+constexpr int tma_tile_y(int S) { return S == 2 ? 10 : 8; }
+
+// CTAs of a TX x TY tile kernel that fit on one SM at once, limited by
+// shared memory (the tile plus halo of 16 S float planes, and 1 KB reserved
+// per CTA) and by registers (at least 64 per thread), at most four: the
+// minimum-blocks bound of the kernel's __launch_bounds__.
+constexpr int tma_ctas_per_sm(int S, int TX, int TY)
+{
+    const int by_smem = (227 * 1024) / ((TX + 8) * (TY + 4) * S * 64 + 1152);
+    const int by_regs = 65536 / (TX * TY * 64);
+    const int n = by_smem < by_regs ? by_smem : by_regs;
+    return n > 4 ? 4 : n < 1 ? 1 : n;
+}
 
 // Launchers; each returns DBM_OK or DBM_ERR_CUDA (message in h->err).
 int launch_step(dbm_handle *h, int cur, cudaStream_t st);

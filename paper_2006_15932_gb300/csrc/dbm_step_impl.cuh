@@ -445,7 +445,7 @@ __device__ __forceinline__ void tma_tile_load(float *tile, unsigned long long tm
 }
 
 template <int S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 2)
+__global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
     k_step_tma(const __grid_constant__ StepConsts<float, S> c, const __grid_constant__ CUtensorMap tmap,
                float *__restrict__ fout, unsigned *__restrict__ flag)
 {
