@@ -36,14 +36,22 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// FP32 storage: f = f^eq(rho^s / m^s, u, T) through the symmetry blocks in
-// FP64 (40 multiply-adds per species instead of the 256 of the full M^-1;
-// the blocks reproduce M^-1 to 1e-13, far below the rounding to float).
+// 1 / m^s in FP64, for the conversion of the FP64 input fields.
+template <int S>
+struct InvMass {
+    double v[S];
+};
+
+// FP32 storage: f = f^eq(rho^s / m^s, u, T) by the step kernel's own FP32
+// symmetry-block solve (with its projection onto exact mass, momentum and
+// energy): the state starts as the equilibrium the FP32 step itself builds,
+// at a fraction of the cost of the FP64 matrix product (a few float ulps
+// from the correctly rounded FP64 equilibrium).
 template <int S>
 __global__ void __launch_bounds__(256)
-    k_set_state_blocks(const __grid_constant__ StepConsts<double, S> c, float *__restrict__ f,
+    k_set_state_blocks(const __grid_constant__ StepConsts<float, S> c, float *__restrict__ f,
                        const double *__restrict__ rho_s, const double *__restrict__ ux,
-                       const double *__restrict__ uy, const double *__restrict__ T)
+                       const double *__restrict__ uy, const double *__restrict__ T, const __grid_constant__ InvMass<S> im_d)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -52,14 +60,15 @@ __global__ void __launch_bounds__(256)
     const long long d = (long long)y * c.nx + x;
     const long long cell = (long long)(y + GY) * c.pitch + (x + GX);
     const Images im = cell_images(x, y, c.nx, c.ny, c.bc_x, c.bc_y);
-    const double u_x = ux[d], u_y = uy[d], t = T[d];
+    const float u_x = (float)ux[d], u_y = (float)uy[d];
+    const double t = T[d];
 #pragma unroll 1
     for (int s = 0; s < S; ++s) {
-        double cb[16], o[16];
-        fhat_blocks<double>(rho_s[s * N + d] * c.inv_m[s], u_x, u_y, t * c.inv_m[s], c.dpi[s], cb);
-        solve_blocks<double>(c, s, cb, o);
+        float cb[16], o[16];
+        fhat_blocks<float>((float)(rho_s[s * N + d] * im_d.v[s]), u_x, u_y, (float)(t * im_d.v[s]), c.dpi[s], cb);
+        solve_blocks<float>(c, s, cb, o);
         for (int i = 0; i < Q; ++i)
-            store_with_images(f + (s * Q + i) * c.plane, cell, x, y, c.pitch, im, (float)feq_of<double>(i, o));
+            store_with_images(f + (s * Q + i) * c.plane, cell, x, y, c.pitch, im, feq_of<float>(i, o));
     }
 }
 
@@ -347,9 +356,11 @@ static void set_state_t(dbm_handle *h, void *f, const double *rho_s, const doubl
 {
     dim3 b(32, 8);
     if (sizeof(real) == 4) {
-        StepConsts<double, S> c;
-        fill_step_consts<double, S>(h, c);
-        k_set_state_blocks<S><<<cell_grid(h, b), b, 0, st>>>(c, (float *)f, rho_s, ux, uy, T);
+        StepConsts<float, S> c;
+        fill_step_consts<float, S>(h, c);
+        InvMass<S> im;
+        for (int s = 0; s < S; ++s) im.v[s] = 1.0 / h->p.sp[s].m;
+        k_set_state_blocks<S><<<cell_grid(h, b), b, 0, st>>>(c, (float *)f, rho_s, ux, uy, T, im);
         return;
     }
     OutConsts<S> c;

@@ -116,6 +116,20 @@ def test_set_state_matches_oracle_equilibrium(D, orc):
     assert rel_linf(s.get_f().cpu().numpy(), f0) <= FP64_TOL
 
 
+def test_fp32_set_state_is_the_equilibrium(D, orc):
+    """FP32 storage starts from the FP32 block solve of f^eq: a few float
+    ulps from the oracle's FP64 equilibrium, and the conserved totals of the
+    oracle's equilibrium to float rounding."""
+    pb = W.random_smooth(41, 17, 3, seed=6, reactive=True)
+    s = D.Solver(pb, "fp32")
+    s.set_state()
+    p, f0 = _oracle_f0(orc, pb)
+    assert rel_linf(s.get_f().cpu().numpy(), f0) <= 1e-6
+    c = s.conservation().cpu().numpy()
+    cr = orc.conservation(p, f0)
+    assert np.max(np.abs(c - cr) / np.maximum(np.abs(cr), 1e-30)) <= 1e-6
+
+
 def test_outputs_fp64(D, orc):
     pb = W.random_smooth(31, 12, 3, seed=8, reactive=True)
     p, f0 = _noneq_f(orc, pb, rel=0.1)
