@@ -121,7 +121,7 @@ def step_kernel_name(pb, precision):
     if precision == "bf16dev":
         return f"k_step_bf16<{pb.ns},64,8>"
     if pb.ns <= 3:
-        tx, ty = {1: (32, 8), 2: (32, 10), 3: (32, 8)}[pb.ns]
+        tx, ty = {1: (64, 4), 2: (32, 7), 3: (32, 8)}[pb.ns]
         return f"k_step_tma<float,{pb.ns},{tx},{ty}>"
     return f"k_step<float,{pb.ns}>"
 

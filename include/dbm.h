@@ -227,14 +227,13 @@ int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes);
 int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t table_bytes, void *stream,
                      dbm_batch **out);
 
-/* Choose the tile shape (32x10, 32x8, 32x16 or 32x12 cells), the launch form (as
+/* Choose the tile shape (32x10, 32x8, 32x16, 32x7 or 64x4 cells), the launch form (as
  * many CTAs as are resident at once, each walking a contiguous range of
- * tiles, or one CTA per tile), whether the tile copies promote L2 fills to
- * 256 bytes and whether ghost images are stored with each value or after
- * each species, whichever step this batch fastest: each choice is timed on
- * `reps` trial launches that read the current states and write
- * only the buffers the next step overwrites, so no state advances.
- * Synchronises the stream. */
+ * tiles, or one CTA per tile) and whether the tile copies promote L2 fills
+ * to 256 bytes, whichever step this batch fastest: each choice is timed on
+ * `reps` trial launches that read the current states and write only the
+ * buffers the next step overwrites, so no state advances.  Synchronises the
+ * stream. */
 int dbm_batch_tune(dbm_batch *b, void *stream, int reps);
 
 /* Advance every instance of the batch by nsteps >= 0 (async on stream). */
@@ -245,19 +244,16 @@ int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int
 
 /* The batch's kernel configuration: tile shape, launch form (1: at most
  * the CTAs resident at once, each over a contiguous range of tiles; 0: one
- * CTA per tile), L2 promotion of the tile copies (1: 256 B; 0: none) and
- * ghost-image policy (1: stored with each value; 0: after each species from
- * the thread's own stores).  Null outputs are skipped. */
-int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote,
-                         int *inline_images);
+ * CTA per tile) and L2 promotion of the tile copies (1: 256 B; 0: none).
+ * Null outputs are skipped. */
+int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote);
 
-/* Set the configuration (a compiled tile shape: 32x10, 32x8, 32x16 or
- * 32x12), rewriting the batch's tables; synchronises the stream.  The tile
+/* Set the configuration (a compiled tile shape: 32x10, 32x8, 32x16,
+ * 32x7 or 64x4), rewriting the batch's tables; synchronises the stream.  The tile
  * shape selects the compiled kernel, so two batches with the same shape
  * give bitwise the same result for the same instance, whatever else they
  * hold.  DBM_ERR_INVALID for a shape that is not compiled. */
-int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, int inline_images,
-                         void *stream);
+int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, void *stream);
 
 const char *dbm_batch_last_error(const dbm_batch *b);
 void dbm_batch_destroy(dbm_batch *b);

@@ -12,8 +12,10 @@
 // the constants read from the constant bank (shared-memory copies of them
 // would compete with the stencil reads).  Pairs of steps are replayed from
 // a CUDA graph in which each chunk is an independent two-launch chain; the
-// tile shape, launch form, L2 promotion and ghost-image policy are chosen by
-// timing (dbm_batch_tune).
+// tile shape, launch form and L2 promotion are chosen by timing
+// (dbm_batch_tune).  Like the single-problem TMA kernel, the batched kernel
+// takes a boundary tile's halo from the interior cells and writes no ghost
+// cells.
 #include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -31,6 +33,7 @@ template <int S>
 struct __align__(128) BatchInst {  // CUtensorMap is 128-byte aligned
     CUtensorMap tmap;
     StepConsts<float, S> c;
+    const float *fin;  // the input buffer (interior cells for a boundary tile's halo)
     float *fout;
     unsigned *flag;
 };
@@ -39,25 +42,45 @@ struct __align__(128) BatchInst {  // CUtensorMap is 128-byte aligned
 // 32764 bytes; the tile-list pointer follows the block).
 constexpr int BATCH_PARAM_BYTES = 32 * 1024 - 256;
 
-// Parameter block of one launch: instances k0 .. k0+n-1 and their tiles
-// t0 .. t0+nt-1 of the device tile list.
+// Parameter block of one launch: n instances that share the constants the
+// step uses many times per cell (`hot`: equilibrium blocks, ring speeds,
+// weights, advection numbers), and their tiles t0 .. t0+nt-1 of the device
+// tile list.  The shared constants stay constant-bank operands in the
+// kernel; each instance's own block supplies only geometry, boundaries,
+// reaction and force.
 template <int S>
 struct BatchChunk {
-    static constexpr int CAP = (BATCH_PARAM_BYTES - 128) / (int)sizeof(BatchInst<S>);
-    int k0, n, t0, nt;
+    static constexpr int HOT_BYTES = ((int)sizeof(StepConsts<float, S>) + 127) / 128 * 128;
+    static constexpr int CAP = (BATCH_PARAM_BYTES - 128 - HOT_BYTES) / (int)sizeof(BatchInst<S>);
+    int n, t0, nt, pad;
+    StepConsts<float, S> hot;
     BatchInst<S> e[CAP];
 };
+// The constants of a block that instances must share to go into one
+// launch: everything but geometry, boundaries, reaction and force, which
+// step_cell reads from the instance's own block.
+template <int S>
+void hot_part(StepConsts<float, S> &c)
+{
+    for (int s = 0; s < S; ++s) c.tau_d[s] = c.tau_a[s] = 0.f;
+    c.k_ov = c.Ea_over_R = c.Qheat = c.src = 0.f;
+    c.fuel = c.oxid = c.has_reaction = c.has_force = 0;
+    c.accel_x = c.accel_y = 0.f;
+    c.nx = c.ny = c.pitch = c.bc_x = c.bc_y = 0;
+    c.plane = 0;
+}
+
 static_assert(sizeof(BatchChunk<1>) <= BATCH_PARAM_BYTES && sizeof(BatchChunk<3>) <= BATCH_PARAM_BYTES,
               "parameter block too large");
 
 // One tile of one instance, as a single 16-byte load.
 struct __align__(16) BatchTile {
-    int k;         // instance (index in the batch)
+    int k;         // instance (index in its launch's parameter block)
     int bx0, by0;  // first interior cell of the tile
     int pad;
 };
 
-template <int S, int TX, int TY, bool INLINE_IMAGES>
+template <int S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
     k_step_batch(const __grid_constant__ BatchChunk<S> P, const BatchTile *__restrict__ tiles)
 {
@@ -82,7 +105,7 @@ __global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
     for (int t = t0; t < t1; ++t, phase ^= 1u) {
         const BatchTile cur = next;
         if (t + 1 < t1) next = tiles[t + 1];
-        const BatchInst<S> &e = P.e[cur.k - P.k0];
+        const BatchInst<S> &e = P.e[cur.k];
         __syncthreads();  // barrier initialised / previous tile no longer read
         if (leader) tma_tile_load(tile, reinterpret_cast<unsigned long long>(&e.tmap), cur.bx0, cur.by0, b, BYTES);
         const bool ok = mbar_wait(b, phase, TMA_WAIT_LIMIT);
@@ -93,23 +116,22 @@ __global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
             mbar_wait(b, phase, TMA_WAIT_LIMIT);
             return;
         }
-        const StepConsts<float, S> &c = e.c;
+        const StepConsts<float, S> &g = e.c;
+        fill_tile_halo<NP, TX, TY>(tile, e.fin, cur.bx0, cur.by0, g.nx, g.ny, g.pitch, g.plane, g.bc_x, g.bc_y,
+                                   ty * TX + tx, TX * TY);
         const int x = cur.bx0 + tx, y = cur.by0 + ty;
-        if (x < c.nx && y < c.ny) {
+        if (x < g.nx && y < g.ny) {
             SmemTile st;
             st.base = tile + (ty + 2) * BX + (tx + 4);
             st.P = BY * BX;
             st.py = BX;
-            StateOutT<INLINE_IMAGES> o{e.fout, c.plane, c.nx, c.ny, c.pitch};
-            step_cell<S>(c, st, x, y, o, e.flag);
+            StateOutNoImages o{e.fout, g.plane};
+            step_cell<S>(P.hot, g, st, x, y, o, e.flag);
         }
     }
 }
 
-// The compiled kernel of species count S, tile shape TX x TY and ghost-image
-// policy (inline: each value's images stored with it, best when most warps
-// hold a boundary cell; otherwise after each species from the thread's own
-// stores).
+// The compiled kernel of species count S and tile shape TX x TY.
 struct BatchKernel {
     const void *fn;
     int tx, ty;
@@ -119,10 +141,9 @@ struct BatchKernel {
 };
 
 template <int S, int TX, int TY>
-BatchKernel batch_kernel(bool inline_images)
+BatchKernel batch_kernel()
 {
-    const void *fn = inline_images ? (const void *)k_step_batch<S, TX, TY, true>
-                                   : (const void *)k_step_batch<S, TX, TY, false>;
+    const void *fn = (const void *)k_step_batch<S, TX, TY>;
     return BatchKernel{fn, TX, TY, (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float), sizeof(BatchChunk<S>),
                        BatchChunk<S>::CAP};
 }
@@ -137,25 +158,25 @@ typedef CUresult (*encode_tiled_fn_b)(CUtensorMap *, CUtensorMapDataType, cuuint
                                       CUtensorMapFloatOOBfill);
 
 // Tile shapes compiled for the batched kernel.
-static const int N_SHAPES = 4;
-static const int SHAPE_TX[N_SHAPES] = {32, 32, 32, 32};
-static const int SHAPE_TY[N_SHAPES] = {10, 8, 16, 12};
+static const int N_SHAPES = 5;
+static const int SHAPE_TX[N_SHAPES] = {32, 32, 32, 32, 64};
+static const int SHAPE_TY[N_SHAPES] = {10, 8, 16, 7, 4};
 
 template <int S>
-static BatchKernel batch_kernel_s(int shape, bool inl)
+static BatchKernel batch_kernel_s(int shape)
 {
     switch (shape) {
-    case 0: return batch_kernel<S, 32, 10>(inl);
-    case 1: return batch_kernel<S, 32, 8>(inl);
-    case 2: return batch_kernel<S, 32, 16>(inl);
-    default: return batch_kernel<S, 32, 12>(inl);
+    case 0: return batch_kernel<S, 32, 10>();
+    case 1: return batch_kernel<S, 32, 8>();
+    case 2: return batch_kernel<S, 32, 16>();
+    case 3: return batch_kernel<S, 32, 7>();
+    default: return batch_kernel<S, 64, 4>();
     }
 }
 
-static BatchKernel batch_kernel_for(int S, int shape, bool inl)
+static BatchKernel batch_kernel_for(int S, int shape)
 {
-    return S == 1 ? batch_kernel_s<1>(shape, inl) : S == 2 ? batch_kernel_s<2>(shape, inl)
-                                                           : batch_kernel_s<3>(shape, inl);
+    return S == 1 ? batch_kernel_s<1>(shape) : S == 2 ? batch_kernel_s<2>(shape) : batch_kernel_s<3>(shape);
 }
 
 struct dbm_batch {
@@ -164,7 +185,6 @@ struct dbm_batch {
     int shape;       // index into SHAPE_TX / SHAPE_TY
     int persistent;  // 1: a launch has at most the CTAs resident at once; 0: one CTA per tile
     int promote;     // 1: the tile copies promote L2 fills to 256 B; 0: no promotion
-    int inline_images;  // 1: ghost images stored with each value; 0: after each species
     int parity;      // steps taken mod 2 since the parameter blocks were written
     int total_tiles;
     int resident;    // CTAs of the current kernel resident at once on the device
@@ -223,8 +243,29 @@ static int write_tables(dbm_batch *b, cudaStream_t st)
         q != cudaDriverEntryPointSuccess || !fn)
         return bfail(b, DBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     encode_tiled_fn_b encode = (encode_tiled_fn_b)fn;
+    // group the instances by their shared ("hot") constants, then cut each
+    // group into launches of at most CAP instances
     const int cap = BatchChunk<S>::CAP;
-    const int nchunks = (n + cap - 1) / cap;
+    std::vector<StepConsts<float, S>> cs(n), hot(n);
+    for (int k = 0; k < n; ++k) {
+        fill_step_consts<float, S>(b->h[k], cs[k]);
+        memcpy(&hot[k], &cs[k], sizeof(hot[k]));  // all bytes, padding included, for memcmp
+        hot_part<S>(hot[k]);
+    }
+    std::vector<std::vector<int>> chunks;
+    std::vector<int> rep;  // an instance of each chunk's group
+    for (int k = 0; k < n; ++k) {
+        int j = -1;
+        for (size_t q = 0; q < chunks.size() && j < 0; ++q)
+            if ((int)chunks[q].size() < cap && !memcmp(&hot[rep[q]], &hot[k], sizeof(hot[k]))) j = (int)q;
+        if (j < 0) {
+            chunks.emplace_back();
+            rep.push_back(k);
+            j = (int)chunks.size() - 1;
+        }
+        chunks[j].push_back(k);
+    }
+    const int nchunks = (int)chunks.size();
     const size_t bytes_all = (size_t)2 * nchunks * sizeof(BatchChunk<S>);
     if (nchunks != b->nchunks || !b->chunks) {
         free(b->chunks);
@@ -236,19 +277,18 @@ static int write_tables(dbm_batch *b, cudaStream_t st)
     b->expected_steps.assign(n, 0);
     b->tiles.clear();
     for (int j = 0; j < nchunks; ++j) {
-        const int k0 = j * cap, k1 = k0 + cap < n ? k0 + cap : n;
         const int t0 = (int)b->tiles.size();
         BatchChunk<S> *blk[2] = {reinterpret_cast<BatchChunk<S> *>(chunk_block(b, j, 0)),
                                  reinterpret_cast<BatchChunk<S> *>(chunk_block(b, j, 1))};
-        for (int k = k0; k < k1; ++k) {
+        for (int local = 0; local < (int)chunks[j].size(); ++local) {
+            const int k = chunks[j][local];
             dbm_handle *h = b->h[k];
             b->expected_steps[k] = h->steps;
-            StepConsts<float, S> c;
-            fill_step_consts<float, S>(h, c);
             const int tiles_x = (h->p.nx + TX - 1) / TX, nt = tiles_x * ((h->p.ny + TY - 1) / TY);
-            for (int u = 0; u < nt; ++u) b->tiles.push_back(BatchTile{k, (u % tiles_x) * TX, (u / tiles_x) * TY, 0});
+            for (int u = 0; u < nt; ++u)
+                b->tiles.push_back(BatchTile{local, (u % tiles_x) * TX, (u / tiles_x) * TY, 0});
             for (int par = 0; par < 2; ++par) {
-                BatchInst<S> &e = blk[par]->e[k - k0];
+                BatchInst<S> &e = blk[par]->e[local];
                 void *in = h->f[h->cur ^ par];
                 const dbm_layout &L = h->lay;
                 cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)(16 * S)};
@@ -260,16 +300,17 @@ static int write_tables(dbm_batch *b, cudaStream_t st)
                            b->promote ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                     return bfail(b, DBM_ERR_CUDA, "tensor map encoding failed");
-                e.c = c;
+                e.c = cs[k];
+                e.fin = (const float *)in;
                 e.fout = (float *)h->f[h->cur ^ par ^ 1];
                 e.flag = (unsigned *)h->scratch;
             }
         }
         for (int par = 0; par < 2; ++par) {
-            blk[par]->k0 = k0;
-            blk[par]->n = k1 - k0;
+            blk[par]->n = (int)chunks[j].size();
             blk[par]->t0 = t0;
             blk[par]->nt = (int)b->tiles.size() - t0;
+            blk[par]->hot = cs[rep[j]];
         }
     }
     b->total_tiles = (int)b->tiles.size();
@@ -282,10 +323,10 @@ static int write_tables(dbm_batch *b, cudaStream_t st)
     return DBM_OK;
 }
 
-// Tiles of chunk j (the count sits in the block header: k0, n, t0, nt).
+// Tiles of chunk j (the count sits in the block header: n, t0, nt).
 static int chunk_tiles(const dbm_batch *b, int j)
 {
-    return reinterpret_cast<const int *>(b->chunks + (size_t)(2 * j) * b->k.chunk_bytes)[3];
+    return reinterpret_cast<const int *>(b->chunks + (size_t)(2 * j) * b->k.chunk_bytes)[2];
 }
 
 static int chunk_grid(const dbm_batch *b, int j)
@@ -363,7 +404,7 @@ static void drop_graphs(dbm_batch *b)
 static int rebuild(dbm_batch *b, cudaStream_t st)
 {
     drop_graphs(b);
-    b->k = batch_kernel_for(b->S, b->shape, b->inline_images != 0);
+    b->k = batch_kernel_for(b->S, b->shape);
     cudaError_t e = cudaFuncSetAttribute(b->k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->k.smem);
     if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
     int dev = 0, sms = 0, per = 0;
@@ -408,7 +449,6 @@ int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t tabl
     b->shape = 0;
     b->persistent = 0;
     b->promote = 1;
-    b->inline_images = 1;
     b->table = table;
     b->table_bytes = table_bytes;
     b->chunks = nullptr;
@@ -442,16 +482,15 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
     cudaStream_t st = (cudaStream_t)stream;
     if (reps < 1) reps = 3;
     float best = 1e30f;
-    int best_shape = 0, best_mode = 0, best_promote = 1, best_inline = 1;
+    int best_shape = 0, best_mode = 0, best_promote = 1;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = DBM_OK;
-    for (int trial = 0; trial < 8 * N_SHAPES && !rc; ++trial) {
-        b->shape = trial >> 3;
+    for (int trial = 0; trial < 4 * N_SHAPES && !rc; ++trial) {
+        b->shape = trial >> 2;
         b->persistent = trial & 1;
         b->promote = (trial >> 1) & 1;
-        b->inline_images = (trial >> 2) & 1;
         rc = rebuild(b, st);
         // a trial step reads the current states and writes the other
         // buffers, which the next real step overwrites: no state advances
@@ -468,7 +507,6 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
             best_shape = b->shape;
             best_mode = b->persistent;
             best_promote = b->promote;
-            best_inline = b->inline_images;
         }
     }
     cudaEventDestroy(e0);
@@ -477,7 +515,6 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
     b->shape = best_shape;
     b->persistent = best_mode;
     b->promote = best_promote;
-    b->inline_images = best_inline;
     return rebuild(b, st);
 }
 
@@ -534,24 +571,19 @@ int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int
     return DBM_OK;
 }
 
-int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote,
-                         int *inline_images)
+int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote)
 {
     if (!b) return DBM_ERR_INVALID;
     if (tile_x) *tile_x = SHAPE_TX[b->shape];
     if (tile_y) *tile_y = SHAPE_TY[b->shape];
     if (persistent) *persistent = b->persistent;
     if (promote) *promote = b->promote;
-    if (inline_images) *inline_images = b->inline_images;
     return DBM_OK;
 }
 
-int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, int inline_images,
-                         void *stream)
+int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, void *stream)
 {
-    if (!b || (persistent != 0 && persistent != 1) || (promote != 0 && promote != 1) ||
-        (inline_images != 0 && inline_images != 1))
-        return DBM_ERR_INVALID;
+    if (!b || (persistent != 0 && persistent != 1) || (promote != 0 && promote != 1)) return DBM_ERR_INVALID;
     int shape = -1;
     for (int sh = 0; sh < N_SHAPES; ++sh)
         if (SHAPE_TX[sh] == tile_x && SHAPE_TY[sh] == tile_y) shape = sh;
@@ -559,7 +591,6 @@ int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, i
     b->shape = shape;
     b->persistent = persistent;
     b->promote = promote;
-    b->inline_images = inline_images;
     return rebuild(b, (cudaStream_t)stream);
 }
 

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(TX *TY, 2)
     t.P = BY * BX;
     t.py = BX;
     BfOut o{out, c.nx, c.ny, c.pitch, S};
-    step_cell<S>(c, t, x, y, o, flag);
+    step_cell<S>(c, c, t, x, y, o, flag);
 }
 
 // State from macroscopic fields: reference moments n^s = rho^s/m^s, u, T

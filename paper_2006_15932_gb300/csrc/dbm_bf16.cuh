@@ -41,7 +41,7 @@ struct BfState {
 // ghost images after a species / the mixture is complete (the thread
 // re-reads its own stores).
 struct BfOut {
-    static constexpr bool kInlineImages = false;
+    static constexpr bool kNoImages = false;
     BfState st;
     int nx, ny, pitch, S;
     __device__ __forceinline__ void put(const Site &w, int p, float g, float e) const
@@ -58,7 +58,6 @@ struct BfOut {
         __stcs(st.mom + (long long)(S + 1) * st.P + w.cell, uy);
         __stcs(st.mom + (long long)(S + 2) * st.P + w.cell, T);
     }
-    __device__ __forceinline__ void image(const Site &, int, float, float) const {}
     __device__ __forceinline__ void images(const Site &w, int s) const
     {
         for (int i = 0; i < Q; ++i) {

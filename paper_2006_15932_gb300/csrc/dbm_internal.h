@@ -93,14 +93,16 @@ struct dbm_handle {
 namespace dbm {
 
 // Tile of the TMA-staged FP32 step (one cell per thread), by species count:
-// 32 x 8 cells for one species (31 KB of shared memory, four CTAs of 256
-// threads per SM), 32 x 10 for two (72 KB, three CTAs of 320 threads), 32 x 8
-// for three (92 KB, two CTAs).  Measured fastest among 64x8, 32x16, 32x12,
-// 32x10, 32x9, 32x7, 40x8, 48x6, 64x6, 64x5, 64x4, 32x20, 128x4 and others
-// on 4096 x 4096 (two species), 4096 x 2048 (one) and 2048 x 2048 (three)
-// grids: more resident CTAs per SM hide each CTA's wait for its tile.
-constexpr int tma_tile_x(int S) { return 32; }
-constexpr int tma_tile_y(int S) { return S == 2 ? 10 : 8; }
+// 64 x 4 cells for one species (4 CTAs of 256 threads per SM), 32 x 7 for two
+// (56 KB of shared memory, four CTAs of 224 threads), 32 x 8 for three
+// (92 KB, two CTAs).  Measured fastest among 32x16, 32x12, 32x10, 32x9,
+// 32x8, 32x7, 32x6, 32x5, 32x4, 40x8, 48x6, 64x8, 64x6, 64x5, 64x4, 128x4
+// and others on 4096 x 4096 (two species) and 4096 x 2048 (one) grids: more
+// resident CTAs per SM hide each CTA's wait for its tile.  For three species
+// 64 x 4 is 3 % faster on 2048 x 2048 but 10 % slower on the 1024 x 256
+// reactive gas, whose halo re-reads (2.25x against 1.9x) come from L2.
+constexpr int tma_tile_x(int S) { return S == 2 ? 32 : S == 1 ? 64 : 32; }
+constexpr int tma_tile_y(int S) { return S == 2 ? 7 : S == 1 ? 4 : 8; }
 
 // CTAs of a TX x TY tile kernel that fit on one SM at once, limited by
 // shared memory (the tile plus halo of 16 S float planes, and 1 KB reserved

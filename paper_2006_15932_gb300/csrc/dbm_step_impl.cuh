@@ -200,24 +200,17 @@ struct Site {
     long long cell;  // element offset of (x, y) in a plane
 };
 
-// Output of the FP32 state: f^{n+1}.  Ghost images either after all 16
-// values of a species are stored (the thread re-reads its own stores: no
-// registers held across the species loop, best where boundary cells are
-// rare) or as each value is stored (INLINE: no re-read latency, best for
-// small grids where most warps hold a boundary cell).
-template <bool INLINE>
-struct StateOutT {
-    static constexpr bool kInlineImages = INLINE;
+// Output of the FP32 state: f^{n+1}, and the ghost images of a species
+// after all 16 of its values are stored (the thread re-reads its own
+// stores: no registers held across the species loop).
+struct StateOut {
+    static constexpr bool kNoImages = false;
     float *f;  // plane 0 of the output buffer
     long long P;
     int nx, ny, pitch;
     __device__ __forceinline__ void put(const Site &w, int p, float g, float) const
     {
         __stcs(f + (long long)p * P + w.cell, g);  // streamed: not re-read this step
-    }
-    __device__ __forceinline__ void image(const Site &w, int p, float g, float) const
-    {
-        store_images(f + (long long)p * P, w.x, w.y, nx, ny, pitch, w.mx, w.my, g);
     }
     __device__ __forceinline__ void put_n(const Site &, int, float) const {}
     __device__ __forceinline__ void put_mix(const Site &, float, float, float) const {}
@@ -230,11 +223,33 @@ struct StateOutT {
     }
     __device__ __forceinline__ void images_mix(const Site &) const {}
 };
-using StateOut = StateOutT<false>;
 
-// The whole update of cell (x, y).
-template <int S, class K, class Tile, class Out>
-__device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int y, const Out &out,
+// Output of the TMA-staged FP32 steps: f^{n+1} only.  These kernels never
+// read the stored ghost cells (a tile at the domain boundary takes its halo
+// from the interior, fill_tile_halo), so they do not write them either.
+struct StateOutNoImages {
+    static constexpr bool kNoImages = true;
+    float *f;  // plane 0 of the output buffer
+    long long P;
+    __device__ __forceinline__ void put(const Site &w, int p, float g, float) const
+    {
+        __stcs(f + (long long)p * P + w.cell, g);
+    }
+    __device__ __forceinline__ void put_n(const Site &, int, float) const {}
+    __device__ __forceinline__ void put_mix(const Site &, float, float, float) const {}
+    __device__ __forceinline__ void images(const Site &, int) const {}
+    __device__ __forceinline__ void images_mix(const Site &) const {}
+};
+
+// The whole update of cell (x, y).  `c` supplies the constants the cell
+// uses many times (equilibrium blocks, ring speeds, weights, advection
+// numbers); `g` the ones it uses once or twice (grid geometry and
+// boundaries, reaction and force).  The single-problem kernels pass the same
+// parameter block twice; the batched kernel passes the launch's shared
+// constants as `c`, so that they stay constant-bank operands, and each
+// instance's own block as `g`.
+template <int S, class K, class G, class Tile, class Out>
+__device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t, int x, int y, const Out &out,
                                           unsigned *__restrict__ flag)
 {
     // 1. species moments, by ring sums
@@ -262,8 +277,8 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
             se += c.qr[s][r] * rs;
         }
         n[s] = sn;
-        if (s == c.fuel) nf = sn;  // selects, no runtime-indexed register array
-        if (s == c.oxid) no = sn;
+        if (s == g.fuel) nf = sn;  // selects, no runtime-indexed register array
+        if (s == g.oxid) no = sn;
         const float lh = c.lam_h[s], ll = c.lam_l[s], kh = c.kap_h[s], kl = c.kap_l[s];
         w += lh * sn + ll * sn;
         wx += lh * sx + ll * sx;
@@ -291,18 +306,19 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
 
     // 3. reaction: omega_ov and T' (state after a time tau^s)
     float om = 0.0f, dT = 0.0f;
-    if (c.has_reaction) {
-        om = c.k_ov * nf * no * expf(-c.Ea_over_R / T);
-        dT = (c.Qheat - 0.5f * T * c.src) * om / (0.5f * cap);
+    if (g.has_reaction) {
+        om = g.k_ov * nf * no * expf(-g.Ea_over_R / T);
+        dT = (g.Qheat - 0.5f * T * g.src) * om / (0.5f * cap);
     }
 
     Site w_;
     w_.x = x;
     w_.y = y;
-    w_.mx = ghost_mask(x, c.nx, c.bc_x);
-    w_.my = ghost_mask(y, c.ny, c.bc_y);
-    w_.cell = (long long)(y + GY) * c.pitch + (x + GX);
-    const bool images = (w_.mx | w_.my) != 0u;
+    constexpr bool kImages = !Out::kNoImages;
+    w_.mx = kImages ? ghost_mask(x, g.nx, g.bc_x) : 0u;
+    w_.my = kImages ? ghost_mask(y, g.ny, g.bc_y) : 0u;
+    w_.cell = (long long)(y + GY) * g.pitch + (x + GX);
+    const bool images = kImages && (w_.mx | w_.my) != 0u;
     out.put_mix(w_, ux, uy, T);
 
     // the species loop is unrolled up to three species: the constants of each
@@ -324,13 +340,13 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
         float cb[16];
         {
             float nr = ns, Ts = T;
-            if (c.has_reaction) {
-                nr = ns + c.tau_a[s] * om;
+            if (g.has_reaction) {
+                nr = ns + g.tau_a[s] * om;
                 if (nr < -1e-6f * a) bad |= DBM_HEALTH_NSTAR;
-                Ts = T + c.tau_d[s] * dT;
+                Ts = T + g.tau_d[s] * dT;
             }
             fhat_blocks<float>(nr, ux, uy, Ts * c.inv_m[s], c.dpi[s], cb);
-            if (c.has_force && ns != 0.0f) {  // an absent species feels no force
+            if (g.has_force && ns != 0.0f) {  // an absent species feels no force
                 float jx = 0, jy = 0, e = 0;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
@@ -341,11 +357,11 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
                 }
                 const float usx = jx / ns, usy = jy / ns;
                 const float th = (e / ns - (usx * usx + usy * usy)) / c.dpi[s];
-                float g[16], h[16];
-                fhat_blocks<float>(ns, usx + c.accel_x * c.tau[s], usy + c.accel_y * c.tau[s], th, c.dpi[s], g);
-                fhat_blocks<float>(ns, usx, usy, th, c.dpi[s], h);
+                float fd[16], fs[16];  // f-hat at u-dagger and at u^s
+                fhat_blocks<float>(ns, usx + g.accel_x * c.tau[s], usy + g.accel_y * c.tau[s], th, c.dpi[s], fd);
+                fhat_blocks<float>(ns, usx, usy, th, c.dpi[s], fs);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) cb[k] += g[k] - h[k];
+                for (int k = 0; k < 16; ++k) cb[k] += fd[k] - fs[k];
             }
         }
         float o[16];
@@ -367,15 +383,10 @@ __device__ __forceinline__ void step_cell(const K &c, const Tile &t, int x, int 
                 d -= c.cdy[s][r] * nnd_diff_neg(t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1), t.ld(p, 0, 2));
             // 6. forward Euler: f + dt/tau (f^eq,tot - f) - dt v . grad f
             const float e = feq_of<float>(i, o);
-            const float g = f0[i] + dtt * (e - f0[i]) - d;
-            out.put(w_, p, g, e);
-            if constexpr (Out::kInlineImages) {
-                if (images) out.image(w_, p, g, e);
-            }
+            const float f1 = f0[i] + dtt * (e - f0[i]) - d;
+            out.put(w_, p, f1, e);
         }
-        if constexpr (!Out::kInlineImages) {
-            if (images) out.images(w_, s);
-        }
+        if (images) out.images(w_, s);
     }
     if (images) out.images_mix(w_);
     if (bad) raise_flag(flag, bad);
@@ -395,7 +406,7 @@ __global__ void __launch_bounds__(256)
     t.P = c.plane;
     t.py = c.pitch;
     StateOut o{fout, c.plane, c.nx, c.ny, c.pitch};
-    step_cell<S>(c, t, x, y, o, flag);
+    step_cell<S>(c, c, t, x, y, o, flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -444,10 +455,57 @@ __device__ __forceinline__ void tma_tile_load(float *tile, unsigned long long tm
         : "memory");
 }
 
+// Halo of a tile that touches the domain boundary, taken from the interior
+// of the input state (periodic: the wrapped cells; outflow: the edge cell)
+// instead of from stored ghost cells.  The tile holds global columns
+// bx0-4 .. bx0+TX+3 and rows by0-2 .. by0+TY+1 of all NP planes; only the
+// cross-shaped stencil reaches into the halo, so the x halo is needed in the
+// tile's interior rows and the y halo in its interior columns.  All threads
+// of the CTA call this (it ends with a barrier when it wrote anything).
+template <int NP, int TX, int TY>
+__device__ __forceinline__ void fill_tile_halo(float *tile, const float *__restrict__ fin, int bx0, int by0, int nx,
+                                               int ny, int pitch, long long plane, int bc_x, int bc_y, int tid,
+                                               int nthr)
+{
+    constexpr int BX = TX + 8, PS = (TY + 4) * BX;
+    // interior cells of the tile: columns bx0 .. x_hi-1, rows by0 .. y_hi-1;
+    // their stencil reads columns bx0-2 .. x_hi+1 and rows by0-2 .. y_hi+1,
+    // so only the ghost columns {-2, -1, nx, nx+1} and rows {-2, -1, ny,
+    // ny+1} inside those ranges are filled (tile column = x - bx0 + 4 stays
+    // within 2 .. TX+5, tile row = y - by0 + 2 within 0 .. TY+3)
+    const int x_hi = min(bx0 + TX, nx), y_hi = min(by0 + TY, ny);
+    const int left = bx0 == 0 ? 2 : 0, right = min(max(x_hi - nx + 2, 0), 2);
+    const int top = by0 == 0 ? 2 : 0, bottom = min(max(y_hi - ny + 2, 0), 2);
+    if (left + right + top + bottom == 0) return;  // uniform over the CTA
+    // x halo, rows by0 .. y_hi-1
+    const int ncx = left + right, rows = y_hi - by0;
+    const int nxi = ncx * rows * NP;
+    for (int it = tid; it < nxi; it += nthr) {
+        const int cidx = it % ncx, r = (it / ncx) % rows, p = it / (ncx * rows);
+        const int xg = cidx < left ? cidx - 2 : nx + (cidx - left);
+        const int xs = bc_x == DBM_BC_PERIODIC ? ((xg % nx) + nx) % nx : min(max(xg, 0), nx - 1);
+        const int y = by0 + r;
+        tile[p * PS + (y - by0 + 2) * BX + (xg - bx0 + 4)] =
+            fin[(long long)p * plane + (long long)(y + GY) * pitch + (xs + GX)];
+    }
+    // y halo, columns bx0 .. x_hi-1
+    const int nry = top + bottom, cols = x_hi - bx0;
+    const int nyi = nry * cols * NP;
+    for (int it = tid; it < nyi; it += nthr) {
+        const int c = it % cols, ridx = (it / cols) % nry, p = it / (cols * nry);
+        const int yg = ridx < top ? ridx - 2 : ny + (ridx - top);
+        const int ys = bc_y == DBM_BC_PERIODIC ? ((yg % ny) + ny) % ny : min(max(yg, 0), ny - 1);
+        const int x = bx0 + c;
+        tile[p * PS + (yg - by0 + 2) * BX + (x - bx0 + 4)] =
+            fin[(long long)p * plane + (long long)(ys + GY) * pitch + (x + GX)];
+    }
+    __syncthreads();
+}
+
 template <int S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
     k_step_tma(const __grid_constant__ StepConsts<float, S> c, const __grid_constant__ CUtensorMap tmap,
-               float *__restrict__ fout, unsigned *__restrict__ flag)
+               const float *__restrict__ fin, float *__restrict__ fout, unsigned *__restrict__ flag)
 {
     constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q;
     constexpr unsigned BYTES = (unsigned)(BX * BY * NP * sizeof(float));
@@ -464,21 +522,25 @@ __global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
     }
     __syncthreads();
     if (leader) tma_tile_load(tile, reinterpret_cast<unsigned long long>(&tmap), bx0, by0, b, BYTES);
-    if (!mbar_wait(b, 0, TMA_WAIT_LIMIT)) {
+    const bool ok = mbar_wait(b, 0, TMA_WAIT_LIMIT);
+    if (__syncthreads_or(!ok)) {
         // the copy did not land: report, give it one more bounded wait so
-        // that no copy is left writing into this block's shared memory, leave
+        // that no copy is left writing into this block's shared memory, and
+        // leave together
         if (leader) raise_flag(flag, DBM_HEALTH_TIMEOUT);
         mbar_wait(b, 0, TMA_WAIT_LIMIT);
         return;
     }
+    fill_tile_halo<NP, TX, TY>(tile, fin, bx0, by0, c.nx, c.ny, c.pitch, c.plane, c.bc_x, c.bc_y, ty * TX + tx,
+                               TX * TY);
     const int x = bx0 + tx, y = by0 + ty;
     if (x >= c.nx || y >= c.ny) return;
     SmemTile t;
     t.base = tile + (ty + 2) * BX + (tx + 4);
     t.P = BY * BX;
     t.py = BX;
-    StateOut o{fout, c.plane, c.nx, c.ny, c.pitch};
-    step_cell<S>(c, t, x, y, o, flag);
+    StateOutNoImages o{fout, c.plane};
+    step_cell<S>(c, c, t, x, y, o, flag);
 }
 
 template <int S>
@@ -493,7 +555,7 @@ int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st)
 }
 
 template <int S, int TX, int TY>
-int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, void *fout, cudaStream_t st)
+int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st)
 {
     constexpr size_t smem = (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float);
     static bool attr_set = false;  // per instantiation, set once per process
@@ -507,7 +569,8 @@ int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, void *fout, cudaSt
     fill_step_consts<float, S>(h, c);
     dim3 block(TX, TY);
     dim3 grid((h->p.nx + TX - 1) / TX, (h->p.ny + TY - 1) / TY);
-    k_step_tma<S, TX, TY><<<grid, block, smem, st>>>(c, *tmap, (float *)fout, (unsigned *)h->scratch);
+    k_step_tma<S, TX, TY><<<grid, block, smem, st>>>(c, *tmap, (const float *)fin, (float *)fout,
+                                                       (unsigned *)h->scratch);
     return set_cuda_error(h, cudaGetLastError(), "TMA step kernel launch");
 }
 

@@ -41,9 +41,8 @@ from . import dbm as D
 from . import workloads as W
 
 # kernel configuration of the batched groups (tile shape, launch form, L2
-# promotion, ghost-image policy): what the tuner picks for instances of
-# 288^2 and 512^2 cells
-DEFAULT_CONFIG = {"tile": (32, 16), "persistent": 0, "promote": 1, "inline_images": 1}
+# promotion): what the tuner picks for instances of 288^2 and 512^2 cells
+DEFAULT_CONFIG = {"tile": (32, 16), "persistent": 0, "promote": 1}
 
 
 class Admission:

@@ -278,13 +278,23 @@ def test_full_size_one_step_sampled(D, orc, which):
 @pytest.mark.parametrize("nx,ny,ns,bc", [(130, 19, 1, (W.PERIODIC, W.PERIODIC)),
                                           (67, 9, 2, (W.OUTFLOW, W.PERIODIC)),
                                           (45, 17, 3, (W.PERIODIC, W.OUTFLOW)),
-                                          (1, 1, 2, (W.PERIODIC, W.PERIODIC))])
+                                          (1, 1, 2, (W.PERIODIC, W.PERIODIC)),
+                                          (33, 21, 2, (W.PERIODIC, W.OUTFLOW)),
+                                          (33, 21, 2, (W.OUTFLOW, W.PERIODIC)),
+                                          (2, 3, 3, (W.PERIODIC, W.PERIODIC)),
+                                          (34, 9, 1, (W.OUTFLOW, W.OUTFLOW)),
+                                          (65, 17, 3, (W.PERIODIC, W.PERIODIC)),
+                                          (65, 5, 1, (W.PERIODIC, W.OUTFLOW)),
+                                          (33, 8, 2, (W.OUTFLOW, W.OUTFLOW))])
 def test_tma_kernel_matches_generic_bitwise(D, orc, nx, ny, ns, bc):
     """The TMA-staged kernel reads its stencil from shared memory and runs
     the same arithmetic as the generic kernel; the two are compiled
     separately, so multiply-add contraction may differ in the last bit:
     after 6 FP32 steps they agree to 1e-6 relative (a wrong tile origin,
-    halo or plane stride would be an O(1) error)."""
+    halo or plane stride would be an O(1) error).  The generic kernel reads
+    the stored ghost cells; the TMA kernel writes none and builds a boundary
+    tile's halo from the interior, so grids one cell past a tile edge, grids
+    smaller than the stencil and every boundary pairing are covered."""
     pb = W.random_smooth(nx, ny, ns, seed=21, reactive=ns == 3, force=ns == 2, bc=bc)
     p, f0 = _noneq_f(orc, pb)
     out = {}
