@@ -3,17 +3,29 @@
 //
 // One CTA steps a TX x TY tile.  Phase A rebuilds f (FP32) of the tile and
 // its radius-2 halo in shared memory from the stored moments and bfloat16
-// deviations; phase B runs the same per-cell FP32 arithmetic as the FP32
+// deviations (a halo cell outside the domain from its periodic or outflow
+// source cell); phase B runs the same per-cell FP32 arithmetic as the FP32
 // kernels (step_cell) on that tile and stores delta^{n+1} and the
-// reference moments.  Reactions and forces are not supported in this
+// reference moments, and no ghost cells.  Reactions and forces are not supported in this
 // storage (their equilibrium is not the one of the stored moments); init
 // rejects them.
 #include "dbm_bf16.cuh"
 
 namespace dbm {
 
+// CTAs of the BF16 step's TX x TY tile that fit on one SM (shared memory for
+// the rebuilt FP32 tile plus its radius-2 halo, at least 64 registers per
+// thread), at most four.
+constexpr int bf16_ctas_per_sm(int S, int TX, int TY)
+{
+    const int by_smem = (227 * 1024) / ((TX + 4) * (TY + 4) * S * 64 + 1024);
+    const int by_regs = 65536 / (TX * TY * 64);
+    const int n = by_smem < by_regs ? by_smem : by_regs;
+    return n > 4 ? 4 : n < 1 ? 1 : n;
+}
+
 template <int S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 2)
+__global__ void __launch_bounds__(TX *TY, bf16_ctas_per_sm(S, TX, TY))
     k_step_bf16(const __grid_constant__ StepConsts<float, S> c, BfState in, BfState out,
                 unsigned *__restrict__ flag)
 {
@@ -24,12 +36,18 @@ __global__ void __launch_bounds__(TX *TY, 2)
     const int nthr = TX * TY, tid = ty * TX + tx;
     const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
 
-    // phase A: rebuild f for the tile and its halo
+    // phase A: rebuild f for the tile and its halo; a halo cell outside the
+    // domain is rebuilt from its source cell (periodic wrap, or the edge cell
+    // for outflow), so the stored ghost cells are neither read nor written
     for (int k = tid; k < BX * BY; k += nthr) {
         const int rr = k / BX, cc = k % BX;
         const int x = bx0 - 2 + cc, y = by0 - 2 + rr;
-        const bool ok = x <= c.nx + 1 && y <= c.ny + 1;  // inside the ghost band
-        const long long cell = (long long)(y + GY) * c.pitch + (x + GX);
+        const bool ok = x <= c.nx + 1 && y <= c.ny + 1;  // within reach of the stencil
+        const int xs = x >= 0 && x < c.nx ? x
+                       : c.bc_x == DBM_BC_PERIODIC ? ((x % c.nx) + c.nx) % c.nx : min(max(x, 0), c.nx - 1);
+        const int ys = y >= 0 && y < c.ny ? y
+                       : c.bc_y == DBM_BC_PERIODIC ? ((y % c.ny) + c.ny) % c.ny : min(max(y, 0), c.ny - 1);
+        const long long cell = (long long)(ys + GY) * c.pitch + (xs + GX);
         float *dst = tile + rr * BX + cc;
 #pragma unroll 1
         for (int s = 0; s < S; ++s) {
@@ -48,7 +66,7 @@ __global__ void __launch_bounds__(TX *TY, 2)
     t.base = tile + (ty + 2) * BX + (tx + 2);
     t.P = BY * BX;
     t.py = BX;
-    BfOut o{out, c.nx, c.ny, c.pitch, S};
+    BfOut o{out, S};
     step_cell<S>(c, c, t, x, y, o, flag);
 }
 
@@ -148,7 +166,7 @@ __global__ void __launch_bounds__(128)
 // launchers
 // ---------------------------------------------------------------------------
 
-constexpr int BF_TX = 64, BF_TY = 8;
+constexpr int BF_TX = 32, BF_TY = 16;  // measured fastest of 64x8, 32x16, 32x8, 32x7 and 64x4
 
 template <int S>
 static int step_bf16_t(dbm_handle *h, int cur, cudaStream_t st)

@@ -37,13 +37,13 @@ struct BfState {
 };
 
 // Output policy of the step: delta^{n+1} = f^{n+1} - f^eq(moments of f^n)
-// (the collision equilibrium the step has just built) and those moments;
-// ghost images after a species / the mixture is complete (the thread
-// re-reads its own stores).
+// (the collision equilibrium the step has just built) and those moments.
+// No ghost cells: the step rebuilds a boundary tile's halo from the source
+// cells (periodic wrap or outflow edge).
 struct BfOut {
-    static constexpr bool kNoImages = false;
+    static constexpr bool kNoImages = true;
     BfState st;
-    int nx, ny, pitch, S;
+    int S;
     __device__ __forceinline__ void put(const Site &w, int p, float g, float e) const
     {
         __stcs(st.d + (long long)p * st.P + w.cell, __float2bfloat16_rn(g - e));
@@ -58,22 +58,8 @@ struct BfOut {
         __stcs(st.mom + (long long)(S + 1) * st.P + w.cell, uy);
         __stcs(st.mom + (long long)(S + 2) * st.P + w.cell, T);
     }
-    __device__ __forceinline__ void images(const Site &w, int s) const
-    {
-        for (int i = 0; i < Q; ++i) {
-            __nv_bfloat16 *pl = st.d + (long long)(s * Q + i) * st.P;
-            store_images(pl, w.x, w.y, nx, ny, pitch, w.mx, w.my, pl[w.cell]);
-        }
-        float *pn = st.mom + (long long)s * st.P;
-        store_images(pn, w.x, w.y, nx, ny, pitch, w.mx, w.my, pn[w.cell]);
-    }
-    __device__ __forceinline__ void images_mix(const Site &w) const
-    {
-        for (int k = S; k < S + 3; ++k) {
-            float *pl = st.mom + (long long)k * st.P;
-            store_images(pl, w.x, w.y, nx, ny, pitch, w.mx, w.my, pl[w.cell]);
-        }
-    }
+    __device__ __forceinline__ void images(const Site &, int) const {}
+    __device__ __forceinline__ void images_mix(const Site &) const {}
 };
 
 // f of species s at one cell (element offset `cell` in a plane), FP32.
