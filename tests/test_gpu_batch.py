@@ -165,3 +165,57 @@ def test_batch_on_the_default_stream(D):
     torch.cuda.synchronize()
     for a, b in zip(solo, mixed):
         assert rel(b.get_f().cpu().numpy(), a.get_f().cpu().numpy()) <= 1e-6
+
+
+def _two_steps_window(orc, p, f0, x0, x1, y0, y1):
+    """Oracle f after two steps on the window [x0,x1) x [y0,y1): the first
+    step on the window grown by the stencil radius (wrapped or clamped by the
+    oracle's own boundary handling), the second on the window."""
+    nx, ny = p.nx, p.ny
+    f1 = f0.copy()
+    gx0, gx1 = max(0, x0 - 2), min(nx, x1 + 2)
+    gy0, gy1 = max(0, y0 - 2), min(ny, y1 + 2)
+    # cells within 2 of the window across a periodic edge wrap around: step
+    # the whole grid rows / columns in that case (small instances only)
+    if p.bc_x == W.PERIODIC and (x0 < 2 or x1 > nx - 2):
+        gx0, gx1 = 0, nx
+    if p.bc_y == W.PERIODIC and (y0 < 2 or y1 > ny - 2):
+        gy0, gy1 = 0, ny
+    reg, st = orc.step_region(p, f0, gx0, gx1, gy0, gy1)
+    assert st == 0
+    f1[:, :, gy0:gy1, gx0:gx1] = reg
+    out, st = orc.step_region(p, f1, x0, x1, y0, y1)
+    assert st == 0
+    return out
+
+
+def test_batched_workload_full_size_sampled(D, orc):
+    """The batched benchmark configuration at full size (64 instances,
+    sides 64..512, shock tubes and reactive gases), tuned and stepped by one
+    two-step graph replay exactly as the benchmark times it; sampled windows
+    of eight instances against the oracle."""
+    pbs = W.batched_instances()
+    stream = torch.cuda.Stream()
+    sols = []
+    for pb in pbs:
+        s = D.Solver(pb, "fp32", stream=stream)
+        s.set_state()
+        sols.append(s)
+    batch = D.Batch(sols, stream=stream, tune=True)
+    f0s = {k: sols[k].get_f().cpu().numpy() for k in range(0, 64, 8)}
+    batch.step(2)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(1)
+    for k, f0 in f0s.items():
+        pb = pbs[k]
+        assert sols[k].status()[0] == 0
+        f2 = sols[k].get_f().cpu().numpy()
+        p = W.to_oracle_params(pb)
+        w = 16
+        corners = [(0, 0), (pb.nx - w, pb.ny - w),
+                   (int(rng.integers(0, pb.nx - w)), int(rng.integers(0, pb.ny - w)))]
+        for x0, y0 in corners:
+            want = _two_steps_window(orc, p, f0, x0, x0 + w, y0, y0 + w)
+            got = f2[:, :, y0:y0 + w, x0:x0 + w]
+            assert rel(got, want) <= 1e-6, (k, x0, y0)
+    batch.close()
