@@ -110,7 +110,12 @@ typedef struct dbm_params {
 
 /* Device storage geometry of one state buffer: plane p = s*16 + i holds
  * `rows` rows of `pitch` elements; interior cell (x, y) sits at element
- * p*plane + (y + gy)*pitch + (x + gx).  Ghost cells fill the margins.
+ * p*plane + (y + gy)*pitch + (x + gx).  The margins hold ghost cells:
+ * dbm_set_state / dbm_set_f fill them, and so do the FP64 step and the
+ * generic FP32 step, which read their boundary stencils from them; the
+ * TMA-staged FP32 step and the BF16DEV step read a boundary cell's stencil
+ * from its periodic or outflow source cell instead and leave the margins
+ * untouched.  Only interior cells carry the state.
  * For DBM_BF16DEV the buffer holds 16*S bfloat16 deviation planes followed
  * (at byte offset moments_offset) by S+3 float moment planes
  * (n^0..n^{S-1}, u_x, u_y, T) of the same geometry. */
@@ -173,7 +178,7 @@ int dbm_get_f(dbm_handle *h, double *f, void *stream);
 
 /* Advance nsteps >= 0 forward-Euler steps (Eqs. DiscreteBoltzmannEquation,
  * CollisionTerm, ReactionTerm, ForceTerm; NND advection).  One fused kernel
- * launch per step; ghosts of the new state are written by the same kernel.
+ * launch per step (boundary conditions inside the same kernel).
  * Async on stream; never synchronises and never allocates. */
 int dbm_step(dbm_handle *h, int nsteps, void *stream);
 
