@@ -32,6 +32,14 @@ METRIC = "D2V16 species-cell updates/s and HBM-roofline %, FP32 vs FP64; serve p
 UNIT = "species-cell updates/s"
 BYTES_PER_UPDATE = {"fp64": 256, "fp32": 128}
 FALLBACK_HBM_GBS = 6800.0
+# The FP64 step (oracle operation order, no fused multiply-add) is bound by
+# the FP64 pipe, not by HBM.  Its FP64 operations per species-cell update,
+# from the ncu counts of one 1024 x 1024 two-species launch (DADD 85.8 +
+# DMUL 80.1 + 2 x DFMA 46.2 flop per cycle over 12.24 ms at 2.06 GHz for
+# 2.10 M updates), and the nominal FP64 peak of a GB300 (no measured FP64
+# figure exists for this pool).
+FP64_FLOPS_PER_UPDATE = 3107.0
+FP64_PEAK_TFLOPS = 1.25
 
 
 def parse():
@@ -582,7 +590,18 @@ def main():
     bytes_per_launch = units * bpu
     achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload, args.precision)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    if args.precision == "fp64":
+        tflops = value * FP64_FLOPS_PER_UPDATE / 1e12
+        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "nominal GB300 FP64 (no measured FP64 peak); the kernel keeps the oracle's "
+                                   "operation order, so separate adds and multiplies fill the FP64 pipe "
+                                   "(84.5 % busy per ncu) at half the flops of fused multiply-adds",
+                    "kernel": step_kernel_name(pb, args.precision), "flops_per_update": FP64_FLOPS_PER_UPDATE,
+                    "hbm_gbs": achieved, "median_launch_ms": statistics.median(per_launch)}
+    else:
+        roofline = None
+    roofline = roofline or {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "kernel": step_kernel_name(pb, args.precision) if args.workload != "batched"
@@ -684,9 +703,10 @@ def measure_fp64(D, pb, dev, stream, steps=10):
     ms = a.elapsed_time(b) / steps
     s.close()
     upd = pb.nx * pb.ny * pb.ns / (ms * 1e-3)
+    tflops = upd * FP64_FLOPS_PER_UPDATE / 1e12
     return {"value": upd, "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "hbm_frac_of_measured": upd * BYTES_PER_UPDATE["fp64"] / 1e9 / measured_peaks()[0],
-            "bound": "alu (FP64 pipe)"}
+            "bound": "alu (FP64 pipe)", "fp64_tflops": tflops, "fp64_frac_of_nominal": tflops / FP64_PEAK_TFLOPS}
 
 
 if __name__ == "__main__":
