@@ -128,8 +128,8 @@ def step_kernel_name(pb, precision):
         return f"k_step_f64<{pb.ns}>"
     if precision == "bf16dev":
         return f"k_step_bf16<{pb.ns},32,16>"
-    if pb.ns <= 3:
-        tx, ty = {1: (64, 4), 2: (32, 7), 3: (32, 8)}[pb.ns]
+    if pb.ns <= 4:
+        tx, ty = {1: (64, 4), 2: (32, 7), 3: (32, 8), 4: (32, 6)}[pb.ns]
         return f"k_step_tma<float,{pb.ns},{tx},{ty}>"
     return f"k_step<float,{pb.ns}>"
 

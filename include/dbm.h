@@ -76,7 +76,7 @@ enum dbm_health_bits {
 
 /* Step kernel selection (dbm_params.step_kernel). */
 enum dbm_step_kernel {
-    DBM_KERNEL_AUTO = 0,     /* TMA-staged where built (FP32, S <= 3), else generic */
+    DBM_KERNEL_AUTO = 0,     /* TMA-staged where built (FP32, S <= 4), else generic */
     DBM_KERNEL_GENERIC = 1,  /* stencil read from global memory                      */
     DBM_KERNEL_TMA = 2       /* tile + halo staged in shared memory by one TMA copy  */
 };
@@ -210,7 +210,7 @@ int dbm_conservation(dbm_handle *h, double *out, void *stream);
 /* ------------------------------------------------------------------------
  * Batches: many independent problems stepped together.
  *
- * A batch groups bound FP32 handles with the same species count S <= 3
+ * A batch groups bound FP32 handles with the same species count S <= 4
  * (grids, boundaries, species constants, reaction and time step may all
  * differ).  Each dbm_batch_step advances every instance: one kernel launch
  * per time step covers the tiles of all instances (each CTA a contiguous
@@ -228,7 +228,7 @@ int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes);
 
 /* Build a batch over n handles; writes the table (async on stream, then
  * synchronises it).  DBM_ERR_INVALID if a handle is unbound, not FP32, has
- * S > 3 or a different S than the others, or the table is too small. */
+ * S > 4 or a different S than the others, or the table is too small. */
 int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t table_bytes, void *stream,
                      dbm_batch **out);
 

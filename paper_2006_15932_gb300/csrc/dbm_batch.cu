@@ -70,7 +70,7 @@ void hot_part(StepConsts<float, S> &c)
     c.plane = 0;
 }
 
-static_assert(sizeof(BatchChunk<1>) <= BATCH_PARAM_BYTES && sizeof(BatchChunk<3>) <= BATCH_PARAM_BYTES,
+static_assert(sizeof(BatchChunk<1>) <= BATCH_PARAM_BYTES && sizeof(BatchChunk<4>) <= BATCH_PARAM_BYTES,
               "parameter block too large");
 
 // One tile of one instance, as a single 16-byte load.
@@ -176,7 +176,8 @@ static BatchKernel batch_kernel_s(int shape)
 
 static BatchKernel batch_kernel_for(int S, int shape)
 {
-    return S == 1 ? batch_kernel_s<1>(shape) : S == 2 ? batch_kernel_s<2>(shape) : batch_kernel_s<3>(shape);
+    return S == 1 ? batch_kernel_s<1>(shape) : S == 2 ? batch_kernel_s<2>(shape)
+           : S == 3 ? batch_kernel_s<3>(shape) : batch_kernel_s<4>(shape);
 }
 
 struct dbm_batch {
@@ -412,7 +413,10 @@ static int rebuild(dbm_batch *b, cudaStream_t st)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, b->k.fn, b->k.tx * b->k.ty, b->k.smem);
     b->resident = sms * (per > 0 ? per : 1);
-    const int rc = b->S == 1 ? write_tables<1>(b, st) : b->S == 2 ? write_tables<2>(b, st) : write_tables<3>(b, st);
+    const int rc = b->S == 1   ? write_tables<1>(b, st)
+                   : b->S == 2 ? write_tables<2>(b, st)
+                   : b->S == 3 ? write_tables<3>(b, st)
+                               : write_tables<4>(b, st);
     if (rc) return rc;
     b->parity = 0;  // the blocks map each handle's current buffer to parity 0
     return DBM_OK;
@@ -424,7 +428,7 @@ int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes)
 {
     if (!handles || n < 1 || !bytes || !handles[0]) return DBM_ERR_INVALID;
     const int S = handles[0]->p.nspecies;
-    if (S > 3) return DBM_ERR_INVALID;
+    if (S > 4) return DBM_ERR_INVALID;
     for (int k = 0; k < n; ++k)
         if (!handles[k]) return DBM_ERR_INVALID;
     *bytes = table_size(handles, n);
@@ -439,7 +443,7 @@ int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t tabl
     const int S = handles[0] ? handles[0]->p.nspecies : 0;
     for (int k = 0; k < n; ++k) {
         const dbm_handle *h = handles[k];
-        if (!h || !h->bound || h->p.precision != DBM_FP32 || h->p.nspecies != S || S > 3 || !h->tma_ok)
+        if (!h || !h->bound || h->p.precision != DBM_FP32 || h->p.nspecies != S || S > 4 || !h->tma_ok)
             return DBM_ERR_INVALID;
     }
     if (table_bytes < table_size(handles, n) || ((uintptr_t)table & 127)) return DBM_ERR_INVALID;

@@ -100,9 +100,12 @@ namespace dbm {
 // and others on 4096 x 4096 (two species) and 4096 x 2048 (one) grids: more
 // resident CTAs per SM hide each CTA's wait for its tile.  For three species
 // 64 x 4 is 3 % faster on 2048 x 2048 but 10 % slower on the 1024 x 256
-// reactive gas, whose halo re-reads (2.25x against 1.9x) come from L2.
-constexpr int tma_tile_x(int S) { return S == 2 ? 32 : S == 1 ? 64 : 32; }
-constexpr int tma_tile_y(int S) { return S == 2 ? 7 : S == 1 ? 4 : 8; }
+// reactive gas, whose halo re-reads (2.25x against 1.9x) come from L2.  Four
+// species: 32 x 6 (102 KB, two CTAs of 192 threads; 29.4 G/s on 2048 x 2048
+// against 22.3 G/s for the generic kernel; 32x4, 64x4, 32x2, 32x3 and 64x2
+// were slower).
+constexpr int tma_tile_x(int S) { return S == 1 ? 64 : 32; }
+constexpr int tma_tile_y(int S) { return S == 1 ? 4 : S == 2 ? 7 : S == 3 ? 8 : 6; }
 
 // CTAs of a TX x TY tile kernel that fit on one SM at once, limited by
 // shared memory (the tile plus halo of 16 S float planes, and 1 KB reserved

@@ -13,7 +13,7 @@ int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st);
 template <int S, int TX, int TY>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st);
 
-bool tma_supported(const dbm_params &p) { return p.precision == DBM_FP32 && p.nspecies <= 3; }
+bool tma_supported(const dbm_params &p) { return p.precision == DBM_FP32 && p.nspecies <= 4; }
 
 static int tma_box(const dbm_params &p, unsigned box[3])
 {
@@ -85,6 +85,7 @@ int launch_step(dbm_handle *h, int cur, cudaStream_t st)
         case 1: return launch_step_tma_t<1, tma_tile_x(1), tma_tile_y(1)>(h, tm, fin, fout, st);
         case 2: return launch_step_tma_t<2, tma_tile_x(2), tma_tile_y(2)>(h, tm, fin, fout, st);
         case 3: return launch_step_tma_t<3, tma_tile_x(3), tma_tile_y(3)>(h, tm, fin, fout, st);
+        case 4: return launch_step_tma_t<4, tma_tile_x(4), tma_tile_y(4)>(h, tm, fin, fout, st);
         }
     }
     if (want == DBM_KERNEL_TMA) return DBM_ERR_INVALID;

@@ -421,7 +421,7 @@ def dbm_batch_table_bytes(handles) -> int:
     v = C.c_size_t()
     rc = load().dbm_batch_table_bytes(arr, len(handles), C.byref(v))
     if rc != OK:
-        raise DbmError(rc, "batch: handles must be bound FP32 handles with the same S <= 3")
+        raise DbmError(rc, "batch: handles must be bound FP32 handles with the same S <= 4")
     return v.value
 
 
@@ -430,7 +430,7 @@ def dbm_batch_create(handles, table: int, table_bytes: int, stream: int = 0) -> 
     b = C.c_void_p()
     rc = load().dbm_batch_create(arr, len(handles), table, table_bytes, stream, C.byref(b))
     if rc != OK:
-        raise DbmError(rc, "batch: handles must be bound FP32 handles with the same S <= 3")
+        raise DbmError(rc, "batch: handles must be bound FP32 handles with the same S <= 4")
     return b.value
 
 

@@ -11,7 +11,7 @@ Requests (``workloads.RequestSpec``) arrive over time.  The server
   done (its initial fields are built on the device, no host copy of a state
   is ever made);
 * groups the running requests by species count, one CUDA stream per group:
-  S <= 3 are stepped together as one ``Batch`` (one launch per step and chunk
+  S <= 4 are stepped together as one ``Batch`` (one launch per step and chunk
   of instances), larger S one instance after the other on the group stream;
 * advances a group in quanta: all members by q = min(quantum, smallest
   number of steps a member still needs), so every request gets exactly its
@@ -139,7 +139,7 @@ class Server:
     """Continuous-batching server on one device (see the module docstring)."""
 
     def __init__(self, device="cuda", hbm_budget: Optional[int] = None, qmax: int = 128,
-                 config: Optional[dict] = None, keep_f: bool = False, max_batch_ns: int = 3):
+                 config: Optional[dict] = None, keep_f: bool = False, max_batch_ns: int = 4):
         import torch
 
         self.torch = torch

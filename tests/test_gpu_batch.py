@@ -117,17 +117,17 @@ def test_batch_rejects_mixed_species_or_precision(D):
             D.Batch(group, stream=stream)
 
 
-@pytest.mark.parametrize("ns,n", [(1, 70), (2, 45), (3, 33)])
+@pytest.mark.parametrize("ns,n", [(1, 70), (2, 45), (3, 33), (4, 27)])
 def test_batch_spanning_several_launch_chunks(D, ns, n):
-    """More instances than one launch's parameter block holds (63, 36 and
-    28 instances for S = 1, 2, 3): the batch runs several chunks per step;
+    """More instances than one launch's parameter block holds (50, 35, 27
+    and 22 instances for S = 1, 2, 3, 4): the batch runs several chunks per step;
     every instance must still match its own single-problem steps."""
     rng = np.random.default_rng(40 + ns)
     pbs = []
     for k in range(n):
         nx, ny = int(rng.integers(5, 41)), int(rng.integers(3, 29))
         bc = (k % 2, (k // 2) % 2)
-        pbs.append(W.random_smooth(nx, ny, ns, seed=100 * ns + k, reactive=(ns == 3 and k % 2 == 0),
+        pbs.append(W.random_smooth(nx, ny, ns, seed=100 * ns + k, reactive=(ns >= 3 and k % 2 == 0),
                                    force=(k % 4 == 1), bc=bc))
     stream = torch.cuda.Stream()
     solo, mixed = [], []

@@ -285,7 +285,9 @@ def test_full_size_one_step_sampled(D, orc, which):
                                           (34, 9, 1, (W.OUTFLOW, W.OUTFLOW)),
                                           (65, 17, 3, (W.PERIODIC, W.PERIODIC)),
                                           (65, 5, 1, (W.PERIODIC, W.OUTFLOW)),
-                                          (33, 8, 2, (W.OUTFLOW, W.OUTFLOW))])
+                                          (33, 8, 2, (W.OUTFLOW, W.OUTFLOW)),
+                                          (37, 13, 4, (W.PERIODIC, W.OUTFLOW)),
+                                          (3, 2, 4, (W.PERIODIC, W.PERIODIC))])
 def test_tma_kernel_matches_generic_bitwise(D, orc, nx, ny, ns, bc):
     """The TMA-staged kernel reads its stencil from shared memory and runs
     the same arithmetic as the generic kernel; the two are compiled
