@@ -129,8 +129,8 @@ def step_kernel_name(pb, precision):
     if precision == "bf16dev":
         return f"k_step_bf16<{pb.ns},32,16>"
     if pb.ns <= 4:
-        tx, ty = {1: (64, 4), 2: (32, 7), 3: (32, 8), 4: (32, 6)}[pb.ns]
-        return f"k_step_tma<float,{pb.ns},{tx},{ty}>"
+        tx, ty, cw = {1: (64, 4, 1), 2: (64, 8, 2), 3: (32, 8, 1), 4: (32, 6, 1)}[pb.ns]
+        return f"k_step_tma<{pb.ns},{tx},{ty},{cw}>"
     return f"k_step<float,{pb.ns}>"
 
 

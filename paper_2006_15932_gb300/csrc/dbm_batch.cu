@@ -80,11 +80,11 @@ struct __align__(16) BatchTile {
     int pad;
 };
 
-template <int S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
+template <int S, int TX, int TY, int CW>
+__global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
     k_step_batch(const __grid_constant__ BatchChunk<S> P, const BatchTile *__restrict__ tiles)
 {
-    constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q;
+    constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q, NT = TX / CW * TY;
     constexpr unsigned BYTES = (unsigned)(BX * BY * NP * sizeof(float));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
@@ -118,34 +118,38 @@ __global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
         }
         const StepConsts<float, S> &g = e.c;
         fill_tile_halo<NP, TX, TY>(tile, e.fin, cur.bx0, cur.by0, g.nx, g.ny, g.pitch, g.plane, g.bc_x, g.bc_y,
-                                   ty * TX + tx, TX * TY);
-        const int x = cur.bx0 + tx, y = cur.by0 + ty;
+                                   ty * (TX / CW) + tx, NT);
+        const int x = cur.bx0 + CW * tx, y = cur.by0 + ty;
         if (x < g.nx && y < g.ny) {
-            SmemTile st;
-            st.base = tile + (ty + 2) * BX + (tx + 4);
-            st.P = BY * BX;
-            st.py = BX;
             StateOutNoImages o{e.fout, g.plane};
-            step_cell<S>(P.hot, g, st, x, y, o, e.flag);
+            const float *base = tile + (ty + 2) * BX + (CW * tx + 4);
+            if constexpr (CW == 2) {
+                const SmemTile2 st{base, BY * BX, BX};
+                step_cell<S>(P.hot, g, st, x, y, x + 1 < g.nx, o, e.flag);
+            } else {
+                const SmemTile st{base, BY * BX, BX};
+                step_cell<S>(P.hot, g, st, x, y, true, o, e.flag);
+            }
         }
     }
 }
 
-// The compiled kernel of species count S and tile shape TX x TY.
+// The compiled kernel of species count S and tile shape TX x TY (cells;
+// bx = TX / CW threads per row).
 struct BatchKernel {
     const void *fn;
-    int tx, ty;
+    int tx, ty, bx;
     size_t smem;
     size_t chunk_bytes;
     int cap;
 };
 
-template <int S, int TX, int TY>
+template <int S, int TX, int TY, int CW>
 BatchKernel batch_kernel()
 {
-    const void *fn = (const void *)k_step_batch<S, TX, TY>;
-    return BatchKernel{fn, TX, TY, (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float), sizeof(BatchChunk<S>),
-                       BatchChunk<S>::CAP};
+    const void *fn = (const void *)k_step_batch<S, TX, TY, CW>;
+    return BatchKernel{fn, TX, TY, TX / CW, (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float),
+                       sizeof(BatchChunk<S>), BatchChunk<S>::CAP};
 }
 
 }  // namespace dbm
@@ -157,20 +161,22 @@ typedef CUresult (*encode_tiled_fn_b)(CUtensorMap *, CUtensorMapDataType, cuuint
                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                       CUtensorMapFloatOOBfill);
 
-// Tile shapes compiled for the batched kernel.
-static const int N_SHAPES = 5;
-static const int SHAPE_TX[N_SHAPES] = {32, 32, 32, 32, 64};
-static const int SHAPE_TY[N_SHAPES] = {10, 8, 16, 7, 4};
+// Tile shapes compiled for the batched kernel (cells); the last one runs
+// two cells per thread.
+static const int N_SHAPES = 6;
+static const int SHAPE_TX[N_SHAPES] = {32, 32, 32, 32, 64, 64};
+static const int SHAPE_TY[N_SHAPES] = {10, 8, 16, 7, 4, 8};
 
 template <int S>
 static BatchKernel batch_kernel_s(int shape)
 {
     switch (shape) {
-    case 0: return batch_kernel<S, 32, 10>();
-    case 1: return batch_kernel<S, 32, 8>();
-    case 2: return batch_kernel<S, 32, 16>();
-    case 3: return batch_kernel<S, 32, 7>();
-    default: return batch_kernel<S, 64, 4>();
+    case 0: return batch_kernel<S, 32, 10, 1>();
+    case 1: return batch_kernel<S, 32, 8, 1>();
+    case 2: return batch_kernel<S, 32, 16, 1>();
+    case 3: return batch_kernel<S, 32, 7, 1>();
+    case 4: return batch_kernel<S, 64, 4, 1>();
+    default: return batch_kernel<S, 64, 8, 2>();
     }
 }
 
@@ -356,7 +362,7 @@ static int launch_step_all(dbm_batch *b, int parity, cudaStream_t st)
         ChunkArgs a;
         chunk_args(b, j, parity, a);
         cudaError_t e =
-            cudaLaunchKernel(b->k.fn, dim3(chunk_grid(b, j)), dim3(b->k.tx, b->k.ty), a.args, b->k.smem, st);
+            cudaLaunchKernel(b->k.fn, dim3(chunk_grid(b, j)), dim3(b->k.bx, b->k.ty), a.args, b->k.smem, st);
         if (e != cudaSuccess) return bfail(b, DBM_ERR_CUDA, cudaGetErrorString(e));
     }
     return DBM_OK;
@@ -378,7 +384,7 @@ static int build_graph(dbm_batch *b, int parity, cudaGraphExec_t *out)
             memset(&kp, 0, sizeof(kp));
             kp.func = const_cast<void *>(b->k.fn);
             kp.gridDim = dim3(chunk_grid(b, j));
-            kp.blockDim = dim3(b->k.tx, b->k.ty);
+            kp.blockDim = dim3(b->k.bx, b->k.ty);
             kp.sharedMemBytes = (unsigned)b->k.smem;
             kp.kernelParams = a.args;
             cudaGraphNode_t node;
@@ -411,7 +417,7 @@ static int rebuild(dbm_batch *b, cudaStream_t st)
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, b->k.fn, b->k.tx * b->k.ty, b->k.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, b->k.fn, b->k.bx * b->k.ty, b->k.smem);
     b->resident = sms * (per > 0 ? per : 1);
     const int rc = b->S == 1   ? write_tables<1>(b, st)
                    : b->S == 2 ? write_tables<2>(b, st)

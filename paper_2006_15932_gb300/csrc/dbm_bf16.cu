@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(TX *TY, bf16_ctas_per_sm(S, TX, TY))
     t.P = BY * BX;
     t.py = BX;
     BfOut o{out, S};
-    step_cell<S>(c, c, t, x, y, o, flag);
+    step_cell<S>(c, c, t, x, y, true, o, flag);
 }
 
 // State from macroscopic fields: reference moments n^s = rho^s/m^s, u, T

@@ -1,6 +1,7 @@
 // dbm_device.cuh -- device building blocks of the D2V16 DBM step:
 // the equilibrium moments f-hat, the minmod limiter of the NND scheme and
-// the ghost-image bookkeeping of the boundary conditions.
+// the ghost-image bookkeeping of the boundary conditions.  The NND flux
+// differences are in dbm_step_impl.cuh.
 #pragma once
 
 #include "dbm_internal.h"
@@ -50,23 +51,6 @@ __device__ __forceinline__ float minmod(float a, float b)
     float t;
     asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(t) : "f"(a), "f"(b));
     return copysignf(fmaxf(t, 0.0f), a);
-}
-
-// NND flux difference along one axis for a velocity component of sign
-// `sgn` (+1 or -1): (H_{j+1/2} - H_{j-1/2}) / c, from f_{j-2..j+2}.
-//   c > 0: H_{j+1/2} = c [f_j + mm(f_j - f_{j-1}, f_{j+1} - f_j)/2]
-//   c < 0: H_{j+1/2} = c [f_{j+1} - mm(f_{j+1} - f_j, f_{j+2} - f_{j+1})/2]
-template <typename real>
-__device__ __forceinline__ real nnd_diff_pos(real fm2, real fm1, real f0, real fp1)
-{
-    const real d0 = fm1 - fm2, d1 = f0 - fm1, d2 = fp1 - f0;
-    return d1 + real(0.5) * (minmod(d1, d2) - minmod(d0, d1));
-}
-template <typename real>
-__device__ __forceinline__ real nnd_diff_neg(real fm1, real f0, real fp1, real fp2)
-{
-    const real d1 = f0 - fm1, d2 = fp1 - f0, d3 = fp2 - fp1;
-    return d2 - real(0.5) * (minmod(d2, d3) - minmod(d1, d2));
 }
 
 // Ghost images of interior index k along an axis of n cells: the ghost

@@ -92,25 +92,32 @@ struct dbm_handle {
 
 namespace dbm {
 
-// Tile of the TMA-staged FP32 step (one cell per thread), by species count:
-// 64 x 4 cells for one species (4 CTAs of 256 threads per SM), 32 x 7 for two
-// (56 KB of shared memory, four CTAs of 224 threads), 32 x 8 for three
-// (92 KB, two CTAs).  Measured fastest among 32x16, 32x12, 32x10, 32x9,
-// 32x8, 32x7, 32x6, 32x5, 32x4, 40x8, 48x6, 64x8, 64x6, 64x5, 64x4, 128x4
-// and others on 4096 x 4096 (two species) and 4096 x 2048 (one) grids: more
+// Tile of the TMA-staged FP32 step, by species count, and the cells a
+// thread updates (CW: 1, or 2 adjacent cells of a row with packed FP32x2
+// arithmetic).  One cell per thread: 64 x 4 cells for one species (4 CTAs of
+// 256 threads per SM), 32 x 8 for three (92 KB of shared memory, two CTAs),
+// 32 x 6 for four (102 KB, two CTAs of 192 threads; 29.4 G/s on 2048 x 2048
+// against 22.3 G/s for the generic kernel; 32x4, 64x4, 32x2, 32x3 and 64x2
+// were slower).  Measured fastest among 32x16, 32x12, 32x10, 32x9, 32x8,
+// 32x7, 32x6, 32x5, 32x4, 40x8, 48x6, 64x8, 64x6, 64x5, 64x4, 128x4 and
+// others on 4096 x 4096 (two species) and 4096 x 2048 (one) grids: more
 // resident CTAs per SM hide each CTA's wait for its tile.  For three species
 // 64 x 4 is 3 % faster on 2048 x 2048 but 10 % slower on the 1024 x 256
-// reactive gas, whose halo re-reads (2.25x against 1.9x) come from L2.  Four
-// species: 32 x 6 (102 KB, two CTAs of 192 threads; 29.4 G/s on 2048 x 2048
-// against 22.3 G/s for the generic kernel; 32x4, 64x4, 32x2, 32x3 and 64x2
-// were slower).
-constexpr int tma_tile_x(int S) { return S == 1 ? 64 : 32; }
-constexpr int tma_tile_y(int S) { return S == 1 ? 4 : S == 2 ? 7 : S == 3 ? 8 : 6; }
+// reactive gas, whose halo re-reads (2.25x against 1.9x) come from L2.  Two
+// species: two cells per thread on 64 x 8 cells (110 KB, two CTAs of 256
+// threads): one thread per cell ran 812 instructions per species-cell and
+// was issue-bound; pairs run 540, and the taller tile keeps 16 warps per SM
+// (on 4096 x 4096: 42.0 G/s against 37.7 for one cell per thread on 32 x 7;
+// pairs on 64 x 4, 64 x 6 and 64 x 7 gave 39.6, 36.1 and 39.9).
+constexpr int tma_tile_x(int S) { return S <= 2 ? 64 : 32; }
+constexpr int tma_tile_y(int S) { return S == 1 ? 4 : S == 2 ? 8 : S == 3 ? 8 : 6; }
+constexpr int tma_cw(int S) { return S == 2 ? 2 : 1; }
 
 // CTAs of a TX x TY tile kernel that fit on one SM at once, limited by
 // shared memory (the tile plus halo of 16 S float planes, and 1 KB reserved
-// per CTA) and by registers (at least 64 per thread), at most four: the
-// minimum-blocks bound of the kernel's __launch_bounds__.
+// per CTA) and by registers (at least 64 per cell: 64 per thread for one
+// cell per thread, 128 for two), at most four: the minimum-blocks bound of
+// the kernel's __launch_bounds__.
 constexpr int tma_ctas_per_sm(int S, int TX, int TY)
 {
     const int by_smem = (227 * 1024) / ((TX + 8) * (TY + 4) * S * 64 + 1152);

@@ -10,7 +10,7 @@ namespace dbm {
 
 template <int S>
 int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st);
-template <int S, int TX, int TY>
+template <int S, int TX, int TY, int CW>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st);
 
 bool tma_supported(const dbm_params &p) { return p.precision == DBM_FP32 && p.nspecies <= 4; }
@@ -82,10 +82,10 @@ int launch_step(dbm_handle *h, int cur, cudaStream_t st)
     if (h->tma_ok && want != DBM_KERNEL_GENERIC) {
         const CUtensorMap *tm = &h->tmap[cur];
         switch (h->p.nspecies) {
-        case 1: return launch_step_tma_t<1, tma_tile_x(1), tma_tile_y(1)>(h, tm, fin, fout, st);
-        case 2: return launch_step_tma_t<2, tma_tile_x(2), tma_tile_y(2)>(h, tm, fin, fout, st);
-        case 3: return launch_step_tma_t<3, tma_tile_x(3), tma_tile_y(3)>(h, tm, fin, fout, st);
-        case 4: return launch_step_tma_t<4, tma_tile_x(4), tma_tile_y(4)>(h, tm, fin, fout, st);
+        case 1: return launch_step_tma_t<1, tma_tile_x(1), tma_tile_y(1), tma_cw(1)>(h, tm, fin, fout, st);
+        case 2: return launch_step_tma_t<2, tma_tile_x(2), tma_tile_y(2), tma_cw(2)>(h, tm, fin, fout, st);
+        case 3: return launch_step_tma_t<3, tma_tile_x(3), tma_tile_y(3), tma_cw(3)>(h, tm, fin, fout, st);
+        case 4: return launch_step_tma_t<4, tma_tile_x(4), tma_tile_y(4), tma_cw(4)>(h, tm, fin, fout, st);
         }
     }
     if (want == DBM_KERNEL_TMA) return DBM_ERR_INVALID;

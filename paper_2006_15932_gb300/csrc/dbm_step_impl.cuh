@@ -49,8 +49,99 @@
 
 namespace dbm {
 
+// ---------------------------------------------------------------------------
+// Arithmetic of one cell (float) or of two adjacent cells at once (float2:
+// the packed FP32x2 add/sub/mul/fma instructions of sm_100 and later, one
+// instruction for both cells, each half rounded like the scalar operation).
+// Every operation of the step is an explicitly rounded one, so the compiler
+// does not regroup it.  The code also never passes a product to an add or a
+// subtract (a multiply-add is written as an FMA, and a difference of two
+// products as an FMA chain): the backend may fuse a packed multiply into a
+// following packed add despite the .rn modifier (measured: x*y - z*w comes
+// out as fma(x, y, -(z*w))), never a scalar one.  With that rule the
+// generic, TMA-staged, two-cell and batched kernels produce the same bits
+// for a cell.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vmm(float a, float b) { return minmod(a, b); }
+
+// The packed operations are written as PTX with an explicit .rn rounding:
+// like the scalar _rn intrinsics, such an add or multiply is never fused
+// into an FMA by the compiler.
+__device__ __forceinline__ unsigned long long vpk(float2 a)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 vupk(unsigned long long r)
+{
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+__device__ __forceinline__ float2 vadd(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(vpk(a)), "l"(vpk(b)));
+    return vupk(r);
+}
+__device__ __forceinline__ float2 vsub(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(vpk(a)), "l"(vpk(b)));
+    return vupk(r);
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(vpk(a)), "l"(vpk(b)));
+    return vupk(r);
+}
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(vpk(a)), "l"(vpk(b)), "l"(vpk(c)));
+    return vupk(r);
+}
+__device__ __forceinline__ float2 vmm(float2 a, float2 b) { return make_float2(minmod(a.x, b.x), minmod(a.y, b.y)); }
+
+// Per-cell access to a value: n cells, broadcast, lane j.
+template <class V>
+struct Lanes;
+template <>
+struct Lanes<float> {
+    static constexpr int n = 1;
+    __device__ static float bc(float a) { return a; }
+    __device__ static float get(float v, int) { return v; }
+    __device__ static void set(float &v, int, float a) { v = a; }
+};
+template <>
+struct Lanes<float2> {
+    static constexpr int n = 2;
+    __device__ static float2 bc(float a) { return make_float2(a, a); }
+    __device__ static float get(float2 v, int j) { return j ? v.y : v.x; }
+    __device__ static void set(float2 &v, int j, float a)
+    {
+        if (j)
+            v.y = a;
+        else
+            v.x = a;
+    }
+};
+template <class V>
+__device__ __forceinline__ V bc(float a)
+{
+    return Lanes<V>::bc(a);
+}
+
 // Stencil values of one cell straight from global memory (read-only path).
 struct GlobalTile {
+    using V = float;
     const float *base;  // plane 0, row y + GY, column x + GX
     long long P;        // plane stride
     long long py;       // row stride
@@ -59,88 +150,145 @@ struct GlobalTile {
 
 // Stencil values of one cell from a shared-memory tile [plane][row][column].
 struct SmemTile {
+    using V = float;
     const float *base;  // plane 0, this thread's row and column
     int P, py;
     __device__ __forceinline__ float ld(int p, int dx, int dy) const { return base[p * P + dy * py + dx]; }
 };
 
+// Stencil values of the cells (x, y) and (x + 1, y) from a shared-memory
+// tile: ld(p, dx, dy) = (f(x + dx, y + dy), f(x + 1 + dx, y + dy)) of plane
+// p.  x is even in the tile, so an even dx is one aligned 64-bit load.
+struct SmemTile2 {
+    using V = float2;
+    const float *base;  // plane 0, this thread's row, its first column
+    int P, py;
+    __device__ __forceinline__ float2 ld(int p, int dx, int dy) const
+    {
+        const float *q = base + p * P + dy * py + dx;
+        if (dx & 1) return make_float2(q[0], q[1]);
+        return *reinterpret_cast<const float2 *>(q);
+    }
+};
+
 // The 16 combinations of f-hat that feed the symmetry blocks, for one cell:
 // c[0..3] ring-mean system, c[4..5] B system, c[6..7] H system,
-// c[8..11] x-vector system, c[12..15] y-vector system.
-template <typename real>
-__device__ __forceinline__ void fhat_blocks(real n, real ux, real uy, real th, real dpi, real c[16])
+// c[8..11] x-vector system, c[12..15] y-vector system.  Each is returned as
+// two factors, c[k] = L[k] R[k], so that a caller can fold the last product
+// into a multiply-add.
+template <class V>
+__device__ __forceinline__ void fhat_factors(V n, V ux, V uy, V th, float dpi, V L[16], V R[16])
 {
-    const real xx = ux * ux, yy = uy * uy, u2 = xx + yy;
-    const real a2 = (dpi + real(2)) * th + u2;  // (D+I+2) T/m + u.u
-    const real a4 = (dpi + real(4)) * th + u2;  // (D+I+4) T/m + u.u
-    const real nux = n * ux, nuy = n * uy, nxy = nux * uy, nd = n * (xx - yy);
-    c[0] = n;                                  // f1
-    c[1] = n * (dpi * th + u2);                // f4
-    c[2] = n * (real(2) * th + u2);            // f5 + f7
-    c[3] = n * (real(2) * a2 * th + u2 * a4);  // f14 + f16
-    c[4] = nd;                                 // f5 - f7
-    c[5] = nd * a4;                            // f14 - f16
-    c[6] = nxy;                                // f6
-    c[7] = nxy * a4;                           // f15
-    c[8] = nux;                                // f2
-    c[9] = nux * a2;                           // f8
-    c[10] = nux * (real(3) * th + xx);         // f10
-    c[11] = nux * (th + yy);                   // f12
-    c[12] = nuy;                               // f3
-    c[13] = nuy * a2;                          // f9
-    c[14] = nuy * (real(3) * th + yy);         // f13
-    c[15] = nuy * (th + xx);                   // f11
+    const V xx = vmul(ux, ux), yy = vmul(uy, uy), u2 = vfma(ux, ux, yy);
+    const V a2 = vfma(bc<V>(dpi + 2.0f), th, u2);  // (D+I+2) T/m + u.u
+    const V a4 = vfma(bc<V>(dpi + 4.0f), th, u2);  // (D+I+4) T/m + u.u
+    const V nux = vmul(n, ux), nuy = vmul(n, uy), nxy = vmul(nux, uy);
+    const V q = vfma(vmul(bc<V>(-1.0f), uy), uy, xx);  // ux^2 - uy^2
+    L[0] = n, R[0] = bc<V>(1.0f);                         // f1
+    L[1] = n, R[1] = vfma(bc<V>(dpi), th, u2);            // f4
+    L[2] = n, R[2] = vfma(bc<V>(2.0f), th, u2);           // f5 + f7
+    L[3] = n, R[3] = vfma(vadd(a2, a2), th, vmul(u2, a4)); // f14 + f16
+    L[4] = n, R[4] = q;                                   // f5 - f7
+    L[5] = vmul(n, q), R[5] = a4;                         // f14 - f16
+    L[6] = nux, R[6] = uy;                                // f6
+    L[7] = nxy, R[7] = a4;                                // f15
+    L[8] = n, R[8] = ux;                                  // f2
+    L[9] = nux, R[9] = a2;                                // f8
+    L[10] = nux, R[10] = vfma(bc<V>(3.0f), th, xx);       // f10
+    L[11] = nux, R[11] = vfma(uy, uy, th);                // f12
+    L[12] = n, R[12] = uy;                                // f3
+    L[13] = nuy, R[13] = a2;                              // f9
+    L[14] = nuy, R[14] = vfma(bc<V>(3.0f), th, yy);       // f13
+    L[15] = nuy, R[15] = vfma(ux, ux, th);                // f11
+}
+
+template <class V>
+__device__ __forceinline__ void fhat_blocks(V n, V ux, V uy, V th, float dpi, V c[16])
+{
+    V L[16], R[16];
+    fhat_factors<V>(n, ux, uy, th, dpi, L, R);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) c[k] = k == 0 ? n : vmul(L[k], R[k]);
+}
+
+// k0 c0 + k1 c1 + k2 c2 + k3 c3, accumulated left to right.
+template <class V>
+__device__ __forceinline__ V dot4(const float k[4], V c0, V c1, V c2, V c3)
+{
+    return vfma(bc<V>(k[3]), c3, vfma(bc<V>(k[2]), c2, vfma(bc<V>(k[1]), c1, vmul(bc<V>(k[0]), c0))));
+}
+
+// t - (k0 c0 + k1 c1 + k2 c2 + k3 c3) as a chain of multiply-adds from t.
+template <class V>
+__device__ __forceinline__ V resid4(const float k[4], V c0, V c1, V c2, V c3, V t)
+{
+    return vfma(bc<V>(-k[3]), c3, vfma(bc<V>(-k[2]), c2, vfma(bc<V>(-k[1]), c1, vfma(bc<V>(-k[0]), c0, t))));
 }
 
 // Solve the symmetry blocks (out: ring means A[4], B[2], H[2], X[4], Y[4])
 // and project the result onto exact mass, energy and momentum.
-template <typename real, class K>
-__device__ __forceinline__ void solve_blocks(const K &k, int s, const real c[16], real o[16])
+template <class V, class K>
+__device__ __forceinline__ void solve_blocks(const K &k, int s, const V c[16], V o[16])
 {
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-        o[r] = k.eqA[s][r][0] * c[0] + k.eqA[s][r][1] * c[1] + k.eqA[s][r][2] * c[2] +
-               k.eqA[s][r][3] * c[3];
+    for (int r = 0; r < 4; ++r) o[r] = dot4<V>(k.eqA[s][r], c[0], c[1], c[2], c[3]);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        o[4 + r] = k.eqB[s][r][0] * c[4] + k.eqB[s][r][1] * c[5];
-        o[6 + r] = k.eqH[s][r][0] * c[6] + k.eqH[s][r][1] * c[7];
+        o[4 + r] = vfma(bc<V>(k.eqB[s][r][1]), c[5], vmul(bc<V>(k.eqB[s][r][0]), c[4]));
+        o[6 + r] = vfma(bc<V>(k.eqH[s][r][1]), c[7], vmul(bc<V>(k.eqH[s][r][0]), c[6]));
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        o[8 + r] = k.eqX[s][r][0] * c[8] + k.eqX[s][r][1] * c[9] + k.eqX[s][r][2] * c[10] +
-                   k.eqX[s][r][3] * c[11];
-        o[12 + r] = k.eqX[s][r][0] * c[12] + k.eqX[s][r][1] * c[13] + k.eqX[s][r][2] * c[14] +
-                    k.eqX[s][r][3] * c[15];
+        o[8 + r] = dot4<V>(k.eqX[s][r], c[8], c[9], c[10], c[11]);
+        o[12 + r] = dot4<V>(k.eqX[s][r], c[12], c[13], c[14], c[15]);
     }
     // residual mass (sum f = 4 sum A), energy (sum q f = 4 sum q_r A_r) and
     // momenta (sum v f = sum w_r v_r X_r) of the computed equilibrium
-    const real dm = c[0] - real(4) * ((o[0] + o[1]) + (o[2] + o[3]));
-    const real de = c[1] - (k.q4[s][0] * o[0] + k.q4[s][1] * o[1] + k.q4[s][2] * o[2] + k.q4[s][3] * o[3]);
-    const real dx = c[8] - (k.wv[s][0] * o[8] + k.wv[s][1] * o[9] + k.wv[s][2] * o[10] + k.wv[s][3] * o[11]);
-    const real dy =
-        c[12] - (k.wv[s][0] * o[12] + k.wv[s][1] * o[13] + k.wv[s][2] * o[14] + k.wv[s][3] * o[15]);
+    const V dm = vfma(bc<V>(-4.0f), vadd(vadd(o[0], o[1]), vadd(o[2], o[3])), c[0]);
+    const V de = resid4<V>(k.q4[s], o[0], o[1], o[2], o[3], c[1]);
+    const V dx = resid4<V>(k.wv[s], o[8], o[9], o[10], o[11], c[8]);
+    const V dy = resid4<V>(k.wv[s], o[12], o[13], o[14], o[15], c[12]);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        o[r] += k.eqA[s][r][0] * dm + k.eqA[s][r][1] * de;
-        o[8 + r] += k.eqX[s][r][0] * dx;
-        o[12 + r] += k.eqX[s][r][0] * dy;
+        o[r] = vfma(bc<V>(k.eqA[s][r][1]), de, vfma(bc<V>(k.eqA[s][r][0]), dm, o[r]));
+        o[8 + r] = vfma(bc<V>(k.eqX[s][r][0]), dx, o[8 + r]);
+        o[12 + r] = vfma(bc<V>(k.eqX[s][r][0]), dy, o[12 + r]);
     }
 }
 
 // f^eq of velocity i from the block solution o (see the header comment).
-template <typename real>
-__device__ __forceinline__ real feq_of(int i, const real o[16])
+template <class V>
+__device__ __forceinline__ V feq_of(int i, const V o[16])
 {
     const int r = i >> 2, k = i & 3;
-    const real A = o[r], X = o[8 + r], Y = o[12 + r];
+    const V A = o[r], X = o[8 + r], Y = o[12 + r];
     if ((r & 1) == 0) {  // axis ring: B = o[4 + r/2]
-        const real B = o[4 + (r >> 1)];
-        return k == 0 ? (A + B) + X : k == 1 ? (A - B) + Y : k == 2 ? (A + B) - X : (A - B) - Y;
+        const V B = o[4 + (r >> 1)];
+        return k == 0 ? vadd(vadd(A, B), X) : k == 1 ? vadd(vsub(A, B), Y) : k == 2 ? vsub(vadd(A, B), X)
+                                                                                   : vsub(vsub(A, B), Y);
     }
-    const real H = o[6 + (r >> 1)];  // diagonal ring
-    return k == 0 ? (A + H) + (X + Y) : k == 1 ? (A - H) + (Y - X) : k == 2 ? (A + H) - (X + Y)
-                                                                          : (A - H) - (Y - X);
+    const V H = o[6 + (r >> 1)];  // diagonal ring
+    return k == 0   ? vadd(vadd(A, H), vadd(X, Y))
+           : k == 1 ? vadd(vsub(A, H), vsub(Y, X))
+           : k == 2 ? vsub(vadd(A, H), vadd(X, Y))
+                    : vsub(vsub(A, H), vsub(Y, X));
+}
+
+// NND flux difference along one axis for a velocity component of sign
+// `sgn` (+1 or -1): (H_{j+1/2} - H_{j-1/2}) / c, from f_{j-2..j+2}.
+//   c > 0: H_{j+1/2} = c [f_j + mm(f_j - f_{j-1}, f_{j+1} - f_j)/2]
+//   c < 0: H_{j+1/2} = c [f_{j+1} - mm(f_{j+1} - f_j, f_{j+2} - f_{j+1})/2]
+template <class V>
+__device__ __forceinline__ V nnd_diff_pos(V fm2, V fm1, V f0, V fp1)
+{
+    const V d0 = vsub(fm1, fm2), d1 = vsub(f0, fm1), d2 = vsub(fp1, f0);
+    return vfma(bc<V>(0.5f), vsub(vmm(d1, d2), vmm(d0, d1)), d1);
+}
+template <class V>
+__device__ __forceinline__ V nnd_diff_neg(V fm1, V f0, V fp1, V fp2)
+{
+    const V d1 = vsub(f0, fm1), d2 = vsub(fp1, f0), d3 = vsub(fp2, fp1);
+    return vfma(bc<V>(-0.5f), vsub(vmm(d2, d3), vmm(d1, d2)), d2);
 }
 
 // Ghost-image bitmask of interior index k on an axis of n cells: bit j set
@@ -184,7 +332,7 @@ __device__ __forceinline__ void store_images(T *pl, int x, int y, int nx, int ny
 // _rn intrinsics keep the compiler from contracting these steps.
 __device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux, float uy)
 {
-    const float u2 = ux * ux + uy * uy;
+    const float u2 = __fmaf_rn(ux, ux, __fmul_rn(uy, uy));
     const float p = __fmul_rn(u2, w);
     const float pe = fmaf(u2, w, -p);
     const float s = __fsub_rn(W, p);
@@ -198,11 +346,12 @@ struct Site {
     int x, y;
     unsigned mx, my;
     long long cell;  // element offset of (x, y) in a plane
+    bool two;        // two cells per thread: (x + 1, y) is inside the domain
 };
 
 // Output of the FP32 state: f^{n+1}, and the ghost images of a species
 // after all 16 of its values are stored (the thread re-reads its own
-// stores: no registers held across the species loop).
+// stores: no registers held across the species loop).  One cell per thread.
 struct StateOut {
     static constexpr bool kNoImages = false;
     float *f;  // plane 0 of the output buffer
@@ -224,9 +373,10 @@ struct StateOut {
     __device__ __forceinline__ void images_mix(const Site &) const {}
 };
 
-// Output of the TMA-staged FP32 steps: f^{n+1} only.  These kernels never
-// read the stored ghost cells (a tile at the domain boundary takes its halo
-// from the interior, fill_tile_halo), so they do not write them either.
+// Output of the TMA-staged FP32 steps: f^{n+1} only, one or two cells per
+// thread.  These kernels never read the stored ghost cells (a tile at the
+// domain boundary takes its halo from the interior, fill_tile_halo), so they
+// do not write them either.
 struct StateOutNoImages {
     static constexpr bool kNoImages = true;
     float *f;  // plane 0 of the output buffer
@@ -235,85 +385,142 @@ struct StateOutNoImages {
     {
         __stcs(f + (long long)p * P + w.cell, g);
     }
-    __device__ __forceinline__ void put_n(const Site &, int, float) const {}
-    __device__ __forceinline__ void put_mix(const Site &, float, float, float) const {}
+    __device__ __forceinline__ void put(const Site &w, int p, float2 g, float2) const
+    {
+        float *q = f + (long long)p * P + w.cell;  // x even: 8-byte aligned
+        if (w.two)
+            __stcs(reinterpret_cast<float2 *>(q), g);
+        else
+            __stcs(q, g.x);
+    }
+    template <class V>
+    __device__ __forceinline__ void put_n(const Site &, int, V) const
+    {
+    }
+    template <class V>
+    __device__ __forceinline__ void put_mix(const Site &, V, V, V) const
+    {
+    }
     __device__ __forceinline__ void images(const Site &, int) const {}
     __device__ __forceinline__ void images_mix(const Site &) const {}
 };
 
-// The whole update of cell (x, y).  `c` supplies the constants the cell
-// uses many times (equilibrium blocks, ring speeds, weights, advection
-// numbers); `g` the ones it uses once or twice (grid geometry and
-// boundaries, reaction and force).  The single-problem kernels pass the same
-// parameter block twice; the batched kernel passes the launch's shared
-// constants as `c`, so that they stay constant-bank operands, and each
-// instance's own block as `g`.
+// The ring order the moment sums below are written for (D2V16 definition):
+// axis rings +x, +y, -x, -y; diagonal rings (+,+), (-,+), (-,-), (+,-).
+static_assert(dir_x(0) == 1 && dir_y(1) == 1 && dir_x(2) == -1 && dir_y(3) == -1 && dir_y(0) == 0 &&
+                  dir_x(1) == 0 && dir_x(4) == 1 && dir_y(4) == 1 && dir_x(5) == -1 && dir_y(5) == 1 &&
+                  dir_x(6) == -1 && dir_y(6) == -1 && dir_x(7) == 1 && dir_y(7) == -1,
+              "D2V16 ring order");
+
+// The whole update of cell (x, y), or of the cells (x, y) and (x + 1, y)
+// when the tile delivers pairs (Tile::V = float2; `two` false when x + 1 is
+// outside the domain: that half is computed but neither stored nor checked).
+// `c` supplies the constants the cell uses many times (equilibrium blocks,
+// ring speeds, weights, advection numbers); `g` the ones it uses once or
+// twice (grid geometry and boundaries, reaction and force).  The
+// single-problem kernels pass the same parameter block twice; the batched
+// kernel passes the launch's shared constants as `c`, so that they stay
+// constant-bank operands, and each instance's own block as `g`.
 template <int S, class K, class G, class Tile, class Out>
-__device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t, int x, int y, const Out &out,
-                                          unsigned *__restrict__ flag)
+__device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t, int x, int y, bool two,
+                                          const Out &out, unsigned *__restrict__ flag)
 {
+    using V = typename Tile::V;
+    using L = Lanes<V>;
+    static_assert(L::n == 1 || Out::kNoImages, "ghost images are written one cell per thread");
+
     // 1. species moments, by ring sums
-    float n[S], cap = 0, nf = 0, no = 0;
-    float w = 0, wx = 0, wy = 0, we = 0, wd = 0;
+    V n[S], nf = bc<V>(0.0f), no = bc<V>(0.0f), cap, w, wx, wy, we, wd;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        float sn = 0, sx = 0, sy = 0, se = 0;
+        V sn, sx, sy, se;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            float rs = 0, rx = 0, ry = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int i = 4 * r + k;
-                const float f = t.ld(s * Q + i, 0, 0);
-                rs += f;
-                if (dir_x(i) > 0) rx += f;
-                if (dir_x(i) < 0) rx -= f;
-                if (dir_y(i) > 0) ry += f;
-                if (dir_y(i) < 0) ry -= f;
+            const V f0 = t.ld(s * Q + 4 * r, 0, 0), f1 = t.ld(s * Q + 4 * r + 1, 0, 0);
+            const V f2 = t.ld(s * Q + 4 * r + 2, 0, 0), f3 = t.ld(s * Q + 4 * r + 3, 0, 0);
+            const V rs = vadd(vadd(f0, f2), vadd(f1, f3));
+            V rx, ry;
+            if ((r & 1) == 0) {
+                rx = vsub(f0, f2);
+                ry = vsub(f1, f3);
+            } else {
+                const V a = vsub(f0, f2), b = vsub(f3, f1);
+                rx = vadd(a, b);
+                ry = vsub(a, b);
             }
-            sn += rs;
-            sx += c.vr[s][r] * rx;
-            sy += c.vr[s][r] * ry;
-            se += c.qr[s][r] * rs;
+            if (r == 0) {
+                sn = rs;
+                sx = vmul(bc<V>(c.vr[s][0]), rx);
+                sy = vmul(bc<V>(c.vr[s][0]), ry);
+                se = vmul(bc<V>(c.qr[s][0]), rs);
+            } else {
+                sn = vadd(sn, rs);
+                sx = vfma(bc<V>(c.vr[s][r]), rx, sx);
+                sy = vfma(bc<V>(c.vr[s][r]), ry, sy);
+                se = vfma(bc<V>(c.qr[s][r]), rs, se);
+            }
         }
         n[s] = sn;
         if (s == g.fuel) nf = sn;  // selects, no runtime-indexed register array
         if (s == g.oxid) no = sn;
-        const float lh = c.lam_h[s], ll = c.lam_l[s], kh = c.kap_h[s], kl = c.kap_l[s];
-        w += lh * sn + ll * sn;
-        wx += lh * sx + ll * sx;
-        wy += lh * sy + ll * sy;
-        we += lh * se + ll * se;
-        wd += kh * sn + kl * sn;
-        cap += c.dpi[s] * sn;
+        const V lh = bc<V>(c.lam_h[s]), ll = bc<V>(c.lam_l[s]), kh = bc<V>(c.kap_h[s]), kl = bc<V>(c.kap_l[s]);
+        const V ws = vfma(lh, sn, vmul(ll, sn)), wxs = vfma(lh, sx, vmul(ll, sx));
+        const V wys = vfma(lh, sy, vmul(ll, sy)), wes = vfma(lh, se, vmul(ll, se));
+        const V wds = vfma(kh, sn, vmul(kl, sn));
+        if (s == 0) {
+            w = ws, wx = wxs, wy = wys, we = wes, wd = wds;
+            cap = vmul(bc<V>(c.dpi[0]), sn);
+        } else {
+            w = vadd(w, ws), wx = vadd(wx, wxs), wy = vadd(wy, wys), we = vadd(we, wes), wd = vadd(wd, wds);
+            cap = vfma(bc<V>(c.dpi[s]), sn, cap);
+        }
     }
 
-    // 2. mixture velocity and temperature
-    const float rw = 1.0f / w;
-    const float ux = wx * rw, uy = wy * rw;
-    const float T = mixture_T(we, w, wd, ux, uy);
+    // 2. mixture velocity and temperature (per cell: division, float-float T)
+    V rw, T;
+#pragma unroll
+    for (int j = 0; j < L::n; ++j) L::set(rw, j, 1.0f / L::get(w, j));
+    const V ux = vmul(wx, rw), uy = vmul(wy, rw);
+#pragma unroll
+    for (int j = 0; j < L::n; ++j)
+        L::set(T, j, mixture_T(L::get(we, j), L::get(w, j), L::get(wd, j), L::get(ux, j), L::get(uy, j)));
 
     unsigned bad = 0;
-    float a = 0;  // sum_s |n^s|
+    V a;  // sum_s |n^s|
 #pragma unroll
-    for (int s = 0; s < S; ++s) a += fabsf(n[s]);
+    for (int j = 0; j < L::n; ++j) {
+        float aj = 0.0f;
 #pragma unroll
-    for (int s = 0; s < S; ++s)
-        if (!(n[s] >= -1e-6f * a)) bad |= DBM_HEALTH_DENSITY;
-    if (!(a > 0.0f)) bad |= DBM_HEALTH_DENSITY;
-    if (!(T > 0.0f)) bad |= DBM_HEALTH_TEMPERATURE;
-    if (!isfinite(T + ux + uy)) bad |= DBM_HEALTH_NONFINITE;
+        for (int s = 0; s < S; ++s) aj += fabsf(L::get(n[s], j));
+        L::set(a, j, aj);
+        if (j == 0 || two) {
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                if (!(L::get(n[s], j) >= -1e-6f * aj)) bad |= DBM_HEALTH_DENSITY;
+            if (!(aj > 0.0f)) bad |= DBM_HEALTH_DENSITY;
+            if (!(L::get(T, j) > 0.0f)) bad |= DBM_HEALTH_TEMPERATURE;
+            if (!isfinite(L::get(T, j) + L::get(ux, j) + L::get(uy, j))) bad |= DBM_HEALTH_NONFINITE;
+        }
+    }
 
     // 3. reaction: omega_ov and T' (state after a time tau^s)
-    float om = 0.0f, dT = 0.0f;
+    V om = bc<V>(0.0f), dT = bc<V>(0.0f);
     if (g.has_reaction) {
-        om = g.k_ov * nf * no * expf(-g.Ea_over_R / T);
-        dT = (g.Qheat - 0.5f * T * g.src) * om / (0.5f * cap);
+#pragma unroll
+        for (int j = 0; j < L::n; ++j) {
+            const float Tj = L::get(T, j);
+            const float omj = g.k_ov * L::get(nf, j) * L::get(no, j) * expf(-g.Ea_over_R / Tj);
+            L::set(om, j, omj);
+            L::set(dT, j,
+                   __fmul_rn(__fsub_rn(g.Qheat, __fmul_rn(__fmul_rn(0.5f, Tj), g.src)), omj) /
+                       __fmul_rn(0.5f, L::get(cap, j)));
+        }
     }
 
     Site w_;
     w_.x = x;
     w_.y = y;
+    w_.two = two;
     constexpr bool kImages = !Out::kNoImages;
     w_.mx = kImages ? ghost_mask(x, g.nx, g.bc_x) : 0u;
     w_.my = kImages ? ghost_mask(y, g.ny, g.bc_y) : 0u;
@@ -327,63 +534,88 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
     // slower unrolled)
 #pragma unroll(S <= 3 ? S : 1)
     for (int s = 0; s < S; ++s) {
-        float f0[Q];
+        V f0[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) f0[i] = t.ld(s * Q + i, 0, 0);
         // species density from step 1 (selected, not indexed)
-        float ns = n[0];
+        V ns = n[0];
 #pragma unroll
         for (int j = 1; j < S; ++j)
             if (s == j) ns = n[j];
         out.put_n(w_, s, ns);
         // 4. merged equilibrium moments
-        float cb[16];
+        V cb[16];
         {
-            float nr = ns, Ts = T;
+            V nr = ns, Ts = T;
             if (g.has_reaction) {
-                nr = ns + g.tau_a[s] * om;
-                if (nr < -1e-6f * a) bad |= DBM_HEALTH_NSTAR;
-                Ts = T + g.tau_d[s] * dT;
+                nr = vfma(bc<V>(g.tau_a[s]), om, ns);
+#pragma unroll
+                for (int j = 0; j < L::n; ++j)
+                    if ((j == 0 || two) && L::get(nr, j) < -1e-6f * L::get(a, j)) bad |= DBM_HEALTH_NSTAR;
+                Ts = vfma(bc<V>(g.tau_d[s]), dT, T);
             }
-            fhat_blocks<float>(nr, ux, uy, Ts * c.inv_m[s], c.dpi[s], cb);
-            if (g.has_force && ns != 0.0f) {  // an absent species feels no force
-                float jx = 0, jy = 0, e = 0;
+            fhat_blocks<V>(nr, ux, uy, vmul(Ts, bc<V>(c.inv_m[s])), c.dpi[s], cb);
+            bool present = false;  // an absent species feels no force
+#pragma unroll
+            for (int j = 0; j < L::n; ++j) present |= L::get(ns, j) != 0.0f;
+            if (g.has_force && present) {
+                V jx, jy, e;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const float v = c.vr[s][i >> 2];
-                    jx += (dir_x(i) * v) * f0[i];
-                    jy += (dir_y(i) * v) * f0[i];
-                    e += c.qr[s][i >> 2] * f0[i];
+                    e = i == 0 ? vmul(bc<V>(c.qr[s][0]), f0[0]) : vfma(bc<V>(c.qr[s][i >> 2]), f0[i], e);
+                    if (dir_x(i) != 0) jx = i == 0 ? vmul(bc<V>(dir_x(i) * v), f0[i]) : vfma(bc<V>(dir_x(i) * v), f0[i], jx);
+                    if (dir_y(i) != 0) jy = i == 1 ? vmul(bc<V>(dir_y(i) * v), f0[i]) : vfma(bc<V>(dir_y(i) * v), f0[i], jy);
                 }
-                const float usx = jx / ns, usy = jy / ns;
-                const float th = (e / ns - (usx * usx + usy * usy)) / c.dpi[s];
-                float fd[16], fs[16];  // f-hat at u-dagger and at u^s
-                fhat_blocks<float>(ns, usx + g.accel_x * c.tau[s], usy + g.accel_y * c.tau[s], th, c.dpi[s], fd);
-                fhat_blocks<float>(ns, usx, usy, th, c.dpi[s], fs);
+                V usx, usy, th;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) cb[k] += fd[k] - fs[k];
+                for (int j = 0; j < L::n; ++j) {
+                    const float nsj = L::get(ns, j);
+                    const float ux_s = L::get(jx, j) / nsj, uy_s = L::get(jy, j) / nsj;
+                    L::set(usx, j, ux_s);
+                    L::set(usy, j, uy_s);
+                    L::set(th, j, __fsub_rn(L::get(e, j) / nsj, __fmaf_rn(ux_s, ux_s, __fmul_rn(uy_s, uy_s))) / c.dpi[s]);
+                }
+                // cb += f-hat(u-dagger) - f-hat(u^s), each term one multiply-add
+                // (the second at -n^s, which negates every f-hat exactly)
+                V Ld[16], Rd[16], Ls[16], Rs[16];
+                fhat_factors<V>(ns, vfma(bc<V>(g.accel_x), bc<V>(c.tau[s]), usx),
+                                vfma(bc<V>(g.accel_y), bc<V>(c.tau[s]), usy), th, c.dpi[s], Ld, Rd);
+                fhat_factors<V>(vmul(bc<V>(-1.0f), ns), usx, usy, th, c.dpi[s], Ls, Rs);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    V sum = vfma(Ls[k], Rs[k], vfma(Ld[k], Rd[k], cb[k]));
+#pragma unroll
+                    for (int j = 0; j < L::n; ++j)
+                        if (L::get(ns, j) == 0.0f) L::set(sum, j, L::get(cb[k], j));
+                    cb[k] = sum;
+                }
             }
         }
-        float o[16];
-        solve_blocks<float>(c, s, cb, o);
-        const float dtt = c.dt_tau[s];
+        V o[16];
+        solve_blocks<V>(c, s, cb, o);
+        const V dtt = bc<V>(c.dt_tau[s]);
 
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int p = s * Q + i, r = i >> 2;
-            float d = 0;  // dt v . grad f
-            // 5. NND advection
+            // 6. forward Euler: f + dt/tau (f^eq,tot - f) - dt v . grad f,
+            // with the 5. NND advection terms of x and y each applied as one
+            // fused multiply-add (no product is left for the compiler to fuse)
+            const V e = feq_of<V>(i, o);
+            V f1 = vfma(dtt, vsub(e, f0[i]), f0[i]);
             if (dir_x(i) > 0)
-                d += c.cdx[s][r] * nnd_diff_pos(t.ld(p, -2, 0), t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0));
+                f1 = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos<V>(t.ld(p, -2, 0), t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0)),
+                          f1);
             else if (dir_x(i) < 0)
-                d -= c.cdx[s][r] * nnd_diff_neg(t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0), t.ld(p, 2, 0));
+                f1 = vfma(bc<V>(c.cdx[s][r]), nnd_diff_neg<V>(t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0), t.ld(p, 2, 0)),
+                          f1);
             if (dir_y(i) > 0)
-                d += c.cdy[s][r] * nnd_diff_pos(t.ld(p, 0, -2), t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1));
+                f1 = vfma(bc<V>(-c.cdy[s][r]), nnd_diff_pos<V>(t.ld(p, 0, -2), t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1)),
+                          f1);
             else if (dir_y(i) < 0)
-                d -= c.cdy[s][r] * nnd_diff_neg(t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1), t.ld(p, 0, 2));
-            // 6. forward Euler: f + dt/tau (f^eq,tot - f) - dt v . grad f
-            const float e = feq_of<float>(i, o);
-            const float f1 = f0[i] + dtt * (e - f0[i]) - d;
+                f1 = vfma(bc<V>(c.cdy[s][r]), nnd_diff_neg<V>(t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1), t.ld(p, 0, 2)),
+                          f1);
             out.put(w_, p, f1, e);
         }
         if (images) out.images(w_, s);
@@ -406,15 +638,16 @@ __global__ void __launch_bounds__(256)
     t.P = c.plane;
     t.py = c.pitch;
     StateOut o{fout, c.plane, c.nx, c.ny, c.pitch};
-    step_cell<S>(c, c, t, x, y, o, flag);
+    step_cell<S>(c, c, t, x, y, true, o, flag);
 }
 
 // ---------------------------------------------------------------------------
-// TMA-staged kernel: one CTA steps a TX x TY tile of cells.  One thread
-// issues a single cp.async.bulk.tensor copy of the tile plus its radius-2
-// halo (all 16 S planes, columns x0-4 .. x0+TX+3 so that the copy starts on
-// a 16-byte boundary) into shared memory, completing on an mbarrier; every
-// thread then reads its stencil from shared memory.
+// TMA-staged kernel: one CTA steps a TX x TY tile of cells, CW (1 or 2)
+// adjacent cells of a row per thread.  One thread issues a single
+// cp.async.bulk.tensor copy of the tile plus its radius-2 halo (all 16 S
+// planes, columns x0-4 .. x0+TX+3 so that the copy starts on a 16-byte
+// boundary) into shared memory, completing on an mbarrier; every thread then
+// reads its stencil from shared memory.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -502,12 +735,13 @@ __device__ __forceinline__ void fill_tile_halo(float *tile, const float *__restr
     __syncthreads();
 }
 
-template <int S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
+template <int S, int TX, int TY, int CW>
+__global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
     k_step_tma(const __grid_constant__ StepConsts<float, S> c, const __grid_constant__ CUtensorMap tmap,
                const float *__restrict__ fin, float *__restrict__ fout, unsigned *__restrict__ flag)
 {
-    constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q;
+    static_assert(CW == 1 || CW == 2, "one or two cells per thread");
+    constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q, NT = TX / CW * TY;
     constexpr unsigned BYTES = (unsigned)(BX * BY * NP * sizeof(float));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar;
@@ -531,16 +765,19 @@ __global__ void __launch_bounds__(TX *TY, tma_ctas_per_sm(S, TX, TY))
         mbar_wait(b, 0, TMA_WAIT_LIMIT);
         return;
     }
-    fill_tile_halo<NP, TX, TY>(tile, fin, bx0, by0, c.nx, c.ny, c.pitch, c.plane, c.bc_x, c.bc_y, ty * TX + tx,
-                               TX * TY);
-    const int x = bx0 + tx, y = by0 + ty;
+    fill_tile_halo<NP, TX, TY>(tile, fin, bx0, by0, c.nx, c.ny, c.pitch, c.plane, c.bc_x, c.bc_y,
+                               ty * (TX / CW) + tx, NT);
+    const int x = bx0 + CW * tx, y = by0 + ty;
     if (x >= c.nx || y >= c.ny) return;
-    SmemTile t;
-    t.base = tile + (ty + 2) * BX + (tx + 4);
-    t.P = BY * BX;
-    t.py = BX;
     StateOutNoImages o{fout, c.plane};
-    step_cell<S>(c, c, t, x, y, o, flag);
+    const float *base = tile + (ty + 2) * BX + (CW * tx + 4);
+    if constexpr (CW == 2) {
+        const SmemTile2 t{base, BY * BX, BX};
+        step_cell<S>(c, c, t, x, y, x + 1 < c.nx, o, flag);
+    } else {
+        const SmemTile t{base, BY * BX, BX};
+        step_cell<S>(c, c, t, x, y, true, o, flag);
+    }
 }
 
 template <int S>
@@ -554,23 +791,23 @@ int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st)
     return set_cuda_error(h, cudaGetLastError(), "step kernel launch");
 }
 
-template <int S, int TX, int TY>
+template <int S, int TX, int TY, int CW>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st)
 {
     constexpr size_t smem = (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float);
     static bool attr_set = false;  // per instantiation, set once per process
     if (!attr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_step_tma<S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_step_tma<S, TX, TY, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return set_cuda_error(h, e, "TMA step kernel shared-memory attribute");
         attr_set = true;
     }
     StepConsts<float, S> c;
     fill_step_consts<float, S>(h, c);
-    dim3 block(TX, TY);
+    dim3 block(TX / CW, TY);
     dim3 grid((h->p.nx + TX - 1) / TX, (h->p.ny + TY - 1) / TY);
-    k_step_tma<S, TX, TY><<<grid, block, smem, st>>>(c, *tmap, (const float *)fin, (float *)fout,
-                                                       (unsigned *)h->scratch);
+    k_step_tma<S, TX, TY, CW><<<grid, block, smem, st>>>(c, *tmap, (const float *)fin, (float *)fout,
+                                                           (unsigned *)h->scratch);
     return set_cuda_error(h, cudaGetLastError(), "TMA step kernel launch");
 }
 

@@ -47,7 +47,7 @@ def test_batch_matches_individual_steps(D):
         assert b.status()[0] == 0
         assert D.dbm_steps_taken(b.h) == 21
         fa, fb = a.get_f().cpu().numpy(), b.get_f().cpu().numpy()
-        assert rel(fb, fa) <= 1e-6
+        assert np.array_equal(fb, fa)  # the same explicitly rounded arithmetic
 
 
 def test_batch_tune_leaves_states_unchanged(D):
@@ -62,7 +62,7 @@ def test_batch_tune_leaves_states_unchanged(D):
     before = [s.get_f().cpu().numpy() for s in sols]
     batch = D.Batch(sols, stream=stream, tune=True)
     info = batch.info()
-    assert info["tile"] in ((32, 10), (32, 8), (32, 16), (32, 7), (64, 4)) and info["tiles"] > 0
+    assert info["tile"] in ((32, 10), (32, 8), (32, 16), (32, 7), (64, 4), (64, 8)) and info["tiles"] > 0
     after = [s.get_f().cpu().numpy() for s in sols]
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
@@ -104,7 +104,7 @@ def test_batch_picks_up_a_reset_handle(D):
         s.step(4 if k == 1 else 9)
     torch.cuda.synchronize()
     for a, b in zip(ref, sols):
-        assert rel(b.get_f().cpu().numpy(), a.get_f().cpu().numpy()) <= 1e-6
+        assert np.array_equal(b.get_f().cpu().numpy(), a.get_f().cpu().numpy())
 
 
 def test_batch_rejects_mixed_species_or_precision(D):
@@ -164,7 +164,7 @@ def test_batch_on_the_default_stream(D):
     batch.step(6)
     torch.cuda.synchronize()
     for a, b in zip(solo, mixed):
-        assert rel(b.get_f().cpu().numpy(), a.get_f().cpu().numpy()) <= 1e-6
+        assert np.array_equal(b.get_f().cpu().numpy(), a.get_f().cpu().numpy())
 
 
 def _two_steps_window(orc, p, f0, x0, x1, y0, y1):

@@ -242,6 +242,67 @@ def test_fp32_conservation_drift(D, orc):
     assert abs(c1[4] - c0[4]) / abs(c0[4]) < 1e-6
 
 
+def _two_species(nx, ny, bc, react, force, seed=23):
+    """Two species on a smooth random state; with ``react`` the one-step
+    reaction A + B -> 2 B (equal masses, so sum a m = 0), with ``force`` a
+    body force: every branch of the two-species step."""
+    pb = W.random_smooth(nx, ny, 2, seed=seed, force=force, bc=bc)
+    if react:
+        for sp in pb.species:
+            sp.m = 1.0
+        pb.species[0].a, pb.species[1].a = -1.0, 1.0
+        pb.fuel, pb.oxid = 0, 1
+        pb.k_ov, pb.Ea_over_R, pb.Q = 2.0e3, 2.0, 1.5
+    return pb
+
+
+@pytest.mark.parametrize("nx,ny,react", [(130, 21, True), (129, 9, False)])
+def test_fp32_two_species_against_oracle(D, orc, nx, ny, react):
+    """The two-species FP32 step (two cells per thread, packed FP32x2
+    arithmetic) against the oracle: tiles of 64 x 4 cells with ragged tails
+    in both directions, an odd nx (the last thread of a row has one cell),
+    reaction and force on."""
+    pb = _two_species(nx, ny, (W.OUTFLOW, W.PERIODIC), react, True)
+    p, f0 = _noneq_f(orc, pb)
+    s = D.Solver(pb, "fp32")
+    s.set_f(f0)
+    s.step(50)
+    f = s.get_f().cpu().numpy()
+    mom = s.moments().cpu().numpy()
+    assert s.status()[0] == 0
+    fr, _ = orc.run(p, f0, 50)
+    mr = orc.moments(p, fr)
+    assert rel_linf(f, fr) <= FP32_TOL_F
+    errs = moments_errors(mom, mr, pb.ns)
+    assert np.all(errs <= 2e-4), errs
+
+
+@pytest.mark.parametrize("nx,ny,bc,react,force", [(130, 11, (W.PERIODIC, W.PERIODIC), False, True),
+                                                  (128, 9, (W.OUTFLOW, W.OUTFLOW), True, False),
+                                                  (66, 7, (W.PERIODIC, W.OUTFLOW), True, True),
+                                                  (129, 6, (W.OUTFLOW, W.PERIODIC), True, True),
+                                                  (2, 2, (W.PERIODIC, W.PERIODIC), False, True),
+                                                  (3, 5, (W.OUTFLOW, W.PERIODIC), True, False),
+                                                  (1, 3, (W.PERIODIC, W.OUTFLOW), False, False),
+                                                  (63, 4, (W.PERIODIC, W.PERIODIC), False, False)])
+def test_pair_kernel_matches_generic(D, orc, nx, ny, bc, react, force):
+    """The two-cells-per-thread kernel against the one-cell generic kernel
+    after 6 steps, bit for bit (each half of a packed FP32x2 operation rounds
+    like the scalar one, and both kernels run the same operations): grids of
+    one and several 64-wide tiles, odd and even nx, every boundary pairing,
+    each branch."""
+    pb = _two_species(nx, ny, bc, react, force)
+    p, f0 = _noneq_f(orc, pb)
+    out = {}
+    for kern in ("generic", "tma"):
+        s = D.Solver(pb, "fp32", step_kernel=kern)
+        s.set_f(f0)
+        s.step(6)
+        out[kern] = s.get_f().cpu().numpy()
+        assert s.status()[0] == 0
+    assert np.array_equal(out["tma"], out["generic"])
+
+
 # ---------------------------------------------------------------------------
 # Full-size workloads: sampled windows of one step at the bench sizes
 # ---------------------------------------------------------------------------
@@ -290,13 +351,13 @@ def test_full_size_one_step_sampled(D, orc, which):
                                           (3, 2, 4, (W.PERIODIC, W.PERIODIC))])
 def test_tma_kernel_matches_generic_bitwise(D, orc, nx, ny, ns, bc):
     """The TMA-staged kernel reads its stencil from shared memory and runs
-    the same arithmetic as the generic kernel; the two are compiled
-    separately, so multiply-add contraction may differ in the last bit:
-    after 6 FP32 steps they agree to 1e-6 relative (a wrong tile origin,
-    halo or plane stride would be an O(1) error).  The generic kernel reads
-    the stored ghost cells; the TMA kernel writes none and builds a boundary
-    tile's halo from the interior, so grids one cell past a tile edge, grids
-    smaller than the stencil and every boundary pairing are covered."""
+    the same explicitly rounded arithmetic as the generic kernel (two cells
+    per thread in packed FP32x2 for two species, one otherwise), so after 6
+    FP32 steps the two states are equal bit for bit.  The generic kernel
+    reads the stored ghost cells; the TMA kernel writes none and builds a
+    boundary tile's halo from the interior, so grids one cell past a tile
+    edge, grids smaller than the stencil and every boundary pairing are
+    covered."""
     pb = W.random_smooth(nx, ny, ns, seed=21, reactive=ns == 3, force=ns == 2, bc=bc)
     p, f0 = _noneq_f(orc, pb)
     out = {}
@@ -306,7 +367,7 @@ def test_tma_kernel_matches_generic_bitwise(D, orc, nx, ny, ns, bc):
         s.step(6)
         out[kern] = s.get_f().cpu().numpy()
         assert s.status()[0] == 0
-    assert rel_linf(out["tma"], out["generic"]) <= 1e-6
+    assert np.array_equal(out["tma"], out["generic"])
 
 
 # ---------------------------------------------------------------------------
@@ -346,8 +407,11 @@ def test_bf16dev_set_state_is_the_equilibrium(D, orc):
     s = D.Solver(pb, "bf16dev")
     s.set_state()
     p, f0 = _oracle_f0(orc, pb)
-    # zero deviation: f is the FP32 equilibrium of the given fields
-    assert rel_linf(s.get_f().cpu().numpy(), f0) <= 1e-6
+    # zero deviation: f is the FP32 equilibrium of the stored FP32 moments.
+    # Rounding n, u and T to float (6e-8 relative each) and forming T/m in
+    # float moves the equilibrium by up to ~20x that (the D2V16 f^eq weighs
+    # T^2 and u^4 terms against each other), so the bound is 2e-6.
+    assert rel_linf(s.get_f().cpu().numpy(), f0) <= 2e-6
 
 
 def test_bf16dev_conservation(D, orc):
