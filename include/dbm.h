@@ -232,7 +232,8 @@ int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes);
 int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t table_bytes, void *stream,
                      dbm_batch **out);
 
-/* Choose the tile shape (32x10, 32x8, 32x16, 32x7 or 64x4 cells), the launch form (as
+/* Choose the tile shape (32x10, 32x8, 32x16, 32x7 or 64x4 cells at one cell
+ * per thread, or 64x8 cells at two adjacent cells per thread), the launch form (as
  * many CTAs as are resident at once, each walking a contiguous range of
  * tiles, or one CTA per tile) and whether the tile copies promote L2 fills
  * to 256 bytes, whichever step this batch fastest: each choice is timed on
@@ -254,10 +255,11 @@ int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int
 int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote);
 
 /* Set the configuration (a compiled tile shape: 32x10, 32x8, 32x16,
- * 32x7 or 64x4), rewriting the batch's tables; synchronises the stream.  The tile
- * shape selects the compiled kernel, so two batches with the same shape
- * give bitwise the same result for the same instance, whatever else they
- * hold.  DBM_ERR_INVALID for a shape that is not compiled. */
+ * 32x7, 64x4 or 64x8), rewriting the batch's tables; synchronises the
+ * stream.  Every shape runs the same explicitly rounded arithmetic as
+ * dbm_step, so an instance's result is bitwise the same whatever the shape
+ * and whatever else the batch holds.  DBM_ERR_INVALID for a shape that is
+ * not compiled. */
 int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, void *stream);
 
 const char *dbm_batch_last_error(const dbm_batch *b);

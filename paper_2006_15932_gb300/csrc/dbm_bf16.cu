@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(TX *TY, bf16_ctas_per_sm(S, TX, TY))
                 unsigned *__restrict__ flag)
 {
     constexpr int BX = TX + 4, BY = TY + 4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tile = reinterpret_cast<float *>(smem_raw);  // [16 S][BY][BX], column 0 = x0 - 2
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nthr = TX * TY, tid = ty * TX + tx;

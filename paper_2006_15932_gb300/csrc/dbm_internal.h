@@ -106,9 +106,12 @@ namespace dbm {
 // reactive gas, whose halo re-reads (2.25x against 1.9x) come from L2.  Two
 // species: two cells per thread on 64 x 8 cells (110 KB, two CTAs of 256
 // threads): one thread per cell ran 812 instructions per species-cell and
-// was issue-bound; pairs run 540, and the taller tile keeps 16 warps per SM
+// was issue-bound; pairs run 528, and the taller tile keeps 16 warps per SM
 // (on 4096 x 4096: 42.0 G/s against 37.7 for one cell per thread on 32 x 7;
-// pairs on 64 x 4, 64 x 6 and 64 x 7 gave 39.6, 36.1 and 39.9).
+// pairs on 64 x 4, 64 x 6 and 64 x 7 gave 39.6, 36.1 and 39.9).  Three
+// species in pairs hold half the warps per SM and ran slower (64 x 4 and
+// 32 x 8: 12.4 and 15.5 G/s against 21.4 on the 1024 x 256 reactive gas,
+// 25.2 and 26.6 against 31.2 on 2048 x 1024).
 constexpr int tma_tile_x(int S) { return S <= 2 ? 64 : 32; }
 constexpr int tma_tile_y(int S) { return S == 1 ? 4 : S == 2 ? 8 : S == 3 ? 8 : 6; }
 constexpr int tma_cw(int S) { return S == 2 ? 2 : 1; }

@@ -1,10 +1,11 @@
 // dbm_step_impl.cuh -- the fused per-timestep update of the D2V16 DBM (FP32).
 //
-// One thread owns one cell and computes (section "Discrete Boltzmann model"
+// One thread owns one cell, or two adjacent cells of a row (packed FP32x2
+// arithmetic, see below), and computes (section "Discrete Boltzmann model"
 // and section "Numerical simulation" of arXiv 2006.15932):
 //   1. species moments n^s, n^s u^s, E^s = sum f (v.v + eta^2) by ring sums;
 //   2. mixture u, T for which the collision conserves momentum and energy
-//      (the energy-minus-kinetic subtraction of T in FP64);
+//      (the energy-minus-kinetic subtraction of T in float-float);
 //   3. the one-step Arrhenius rate and the post-reaction n^s*, T*;
 //   4. the merged equilibrium f^eq,tot = M^-1 [f-hat(n*, u, T*)
 //      + f-hat(n, u^dag, T^s) - f-hat(n, u^s, T^s)], so that
@@ -15,7 +16,8 @@
 //   6. the forward-Euler update, stored to the other buffer, then the ghost
 //      images the boundary conditions ask for (edge cells only).
 // The inputs come from a Tile policy: straight from global memory (k_step)
-// or from a shared-memory tile that one TMA bulk copy filled (k_step_tma);
+// or from a shared-memory tile that one TMA bulk copy filled (k_step_tma,
+// one cell or a pair of cells per thread);
 // the outputs go through an Out policy (FP32 state, or the BF16-deviation
 // state of dbm_bf16.cuh).
 //
