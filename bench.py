@@ -122,16 +122,17 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def step_kernel_name(pb, precision):
-    """The step kernel dbm_step dispatches for this problem (DBM_KERNEL_AUTO)."""
+def step_kernel_name(pb, precision, solver):
+    """The step kernel dbm_step dispatches for this problem (DBM_KERNEL_AUTO);
+    the TMA tile as the library reports it."""
     if precision == "fp64":
         return f"k_step_f64<{pb.ns}>"
     if precision == "bf16dev":
         return f"k_step_bf16<{pb.ns},32,16>"
-    if pb.ns <= 4:
-        tx, ty, cw = {1: (64, 4, 1), 2: (64, 8, 2), 3: (32, 8, 1), 4: (32, 6, 1)}[pb.ns]
+    tx, ty, cw = solver.step_tile()
+    if tx:
         return f"k_step_tma<{pb.ns},{tx},{ty},{cw}>"
-    return f"k_step<float,{pb.ns}>"
+    return f"k_step<{pb.ns}>"
 
 
 def ncu_traffic(name, precision):
@@ -597,14 +598,14 @@ def main():
                     "peak_source": "nominal GB300 FP64 (no measured FP64 peak); the kernel keeps the oracle's "
                                    "operation order, so separate adds and multiplies fill the FP64 pipe "
                                    "(84.5 % busy per ncu) at half the flops of fused multiply-adds",
-                    "kernel": step_kernel_name(pb, args.precision), "flops_per_update": FP64_FLOPS_PER_UPDATE,
+                    "kernel": step_kernel_name(pb, args.precision, solver), "flops_per_update": FP64_FLOPS_PER_UPDATE,
                     "hbm_gbs": achieved, "median_launch_ms": statistics.median(per_launch)}
     else:
         roofline = None
     roofline = roofline or {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": step_kernel_name(pb, args.precision) if args.workload != "batched"
+                "kernel": step_kernel_name(pb, args.precision, solver) if args.workload != "batched"
                 else f"k_step_batch<{pb.ns},{cfg['tile'][0]},{cfg['tile'][1]}>",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "median_launch_ms": statistics.median(per_launch)}

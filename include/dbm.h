@@ -74,11 +74,18 @@ enum dbm_health_bits {
     DBM_HEALTH_TIMEOUT = 16      /* a tile copy did not complete within its wait limit */
 };
 
-/* Step kernel selection (dbm_params.step_kernel). */
+/* Step kernel selection (dbm_params.step_kernel).  Every choice runs the
+ * same explicitly rounded arithmetic and gives bitwise identical results;
+ * they differ in speed only. */
 enum dbm_step_kernel {
-    DBM_KERNEL_AUTO = 0,     /* TMA-staged where built (FP32, S <= 4), else generic */
-    DBM_KERNEL_GENERIC = 1,  /* stencil read from global memory                      */
-    DBM_KERNEL_TMA = 2       /* tile + halo staged in shared memory by one TMA copy  */
+    DBM_KERNEL_AUTO = 0,      /* TMA-staged where built (FP32, S <= 4), else generic;
+                                 tile as DBM_KERNEL_TMA                              */
+    DBM_KERNEL_GENERIC = 1,   /* stencil read from global memory                      */
+    DBM_KERNEL_TMA = 2,       /* tile + halo staged in shared memory by one TMA copy;
+                                 for S = 2 two cells per thread on grids of at least
+                                 4096 tiles of 64 x 8 cells, else one cell per thread */
+    DBM_KERNEL_TMA_CELL = 3,  /* TMA-staged, one cell per thread                      */
+    DBM_KERNEL_TMA_PAIR = 4   /* TMA-staged, two adjacent cells per thread (S = 2)    */
 };
 
 /* Constants of one species sigma. */
@@ -104,7 +111,7 @@ typedef struct dbm_params {
     double Q;               /* heat released per mole of reaction                   */
     double accel[2];        /* external acceleration a of the force term; 0 = off   */
     int precision;          /* dbm_precision                                         */
-    int step_kernel;        /* dbm_step_kernel; both give bitwise identical results  */
+    int step_kernel;        /* dbm_step_kernel; all give bitwise identical results   */
     dbm_species sp[DBM_MAX_SPECIES];
 } dbm_params;
 
@@ -301,6 +308,14 @@ int dbm_status(dbm_handle *h, void *stream, unsigned *bits);
 
 /* Steps taken since the last dbm_set_state / dbm_set_f. */
 long long dbm_steps_taken(const dbm_handle *h);
+
+/* The shared-memory tile the step of a bound handle uses (chosen at
+ * dbm_bind from dbm_params.step_kernel and the grid): tile_x x tile_y
+ * cells, cells_per_thread 1 or 2 (adjacent cells of a row, packed FP32x2
+ * arithmetic); all three 0 when the step runs a kernel without a tile
+ * (generic global-memory stencil, FP64, BF16DEV).  Null outputs are
+ * skipped.  DBM_ERR_UNBOUND before dbm_bind. */
+int dbm_step_tile(const dbm_handle *h, int *tile_x, int *tile_y, int *cells_per_thread);
 
 /* Message of the last failed call on this handle ("" if none).  The string
  * is owned by the handle. */

@@ -260,10 +260,13 @@ static int validate(dbm_handle *h, const dbm_params &p)
     }
     if (p.precision != DBM_FP64 && p.precision != DBM_FP32 && p.precision != DBM_BF16DEV)
         return fail(h, DBM_ERR_INVALID, "unknown precision %d", p.precision);
-    if (p.step_kernel < DBM_KERNEL_AUTO || p.step_kernel > DBM_KERNEL_TMA)
+    if (p.step_kernel < DBM_KERNEL_AUTO || p.step_kernel > DBM_KERNEL_TMA_PAIR)
         return fail(h, DBM_ERR_INVALID, "unknown step kernel %d", p.step_kernel);
+    if (p.step_kernel == DBM_KERNEL_TMA_PAIR && (p.precision != DBM_FP32 || p.nspecies != 2))
+        return fail(h, DBM_ERR_INVALID, "the two-cells-per-thread step is built for FP32 with two species");
+    const bool tma_kind = p.step_kernel != DBM_KERNEL_AUTO && p.step_kernel != DBM_KERNEL_GENERIC;
     if (p.precision == DBM_BF16DEV &&
-        (p.nspecies > 4 || p.k_ov != 0.0 || p.accel[0] != 0.0 || p.accel[1] != 0.0 || p.step_kernel == DBM_KERNEL_TMA))
+        (p.nspecies > 4 || p.k_ov != 0.0 || p.accel[0] != 0.0 || p.accel[1] != 0.0 || tma_kind))
         return fail(h, DBM_ERR_INVALID,
                     "BF16DEV storage is built for up to 4 species without reaction or force "
                     "(its reference equilibrium is that of the stored moments)");
@@ -459,8 +462,9 @@ int dbm_bind(dbm_handle *h, void *f_a, void *f_b, void *scratch)
     h->cur = 0;
     h->bound = 1;
     make_tensor_maps(h);
-    if (h->p.step_kernel == DBM_KERNEL_TMA && !h->tma_ok)
-        return fail(h, DBM_ERR_INVALID, "the TMA-staged step kernel is built for FP32 with at most 3 species");
+    const int want = h->p.step_kernel;
+    if (want != DBM_KERNEL_AUTO && want != DBM_KERNEL_GENERIC && !h->tma_ok)
+        return fail(h, DBM_ERR_INVALID, "the TMA-staged step kernel is built for FP32 with at most 4 species");
     return DBM_OK;
 }
 
@@ -581,6 +585,17 @@ int dbm_status(dbm_handle *h, void *stream, unsigned *bits)
 }
 
 long long dbm_steps_taken(const dbm_handle *h) { return h ? h->steps : -1; }
+
+int dbm_step_tile(const dbm_handle *h, int *tile_x, int *tile_y, int *cells_per_thread)
+{
+    if (!h) return DBM_ERR_INVALID;
+    if (!h->bound) return DBM_ERR_UNBOUND;
+    const bool tiled = h->tma_ok && h->p.step_kernel != DBM_KERNEL_GENERIC;
+    if (tile_x) *tile_x = tiled ? h->tma_tx : 0;
+    if (tile_y) *tile_y = tiled ? h->tma_ty : 0;
+    if (cells_per_thread) *cells_per_thread = tiled ? h->tma_cw : 0;
+    return DBM_OK;
+}
 
 const char *dbm_last_error(const dbm_handle *h) { return h ? h->err : "null handle"; }
 

@@ -76,6 +76,8 @@ struct dbm_handle {
     dbm_params p;
     CUtensorMap tmap[2];  // TMA descriptors of the two bound state buffers
     int tma_ok;           // the TMA-staged step kernel can run
+    int tma_tx, tma_ty;   // its tile (cells) and cells per thread (1 or 2),
+    int tma_cw;           // fixed at dbm_bind
     double cinv[DBM_MAX_SPECIES][16][16];  // host FP64 M^-1 per species
     double eqA[DBM_MAX_SPECIES][4][4];     // symmetry blocks of M^-1
     double eqB[DBM_MAX_SPECIES][2][2];
@@ -104,17 +106,22 @@ namespace dbm {
 // resident CTAs per SM hide each CTA's wait for its tile.  For three species
 // 64 x 4 is 3 % faster on 2048 x 2048 but 10 % slower on the 1024 x 256
 // reactive gas, whose halo re-reads (2.25x against 1.9x) come from L2.  Two
-// species: two cells per thread on 64 x 8 cells (110 KB, two CTAs of 256
-// threads): one thread per cell ran 812 instructions per species-cell and
-// was issue-bound; pairs run 528, and the taller tile keeps 16 warps per SM
-// (on 4096 x 4096: 42.0 G/s against 37.7 for one cell per thread on 32 x 7;
-// pairs on 64 x 4, 64 x 6 and 64 x 7 gave 39.6, 36.1 and 39.9).  Three
-// species in pairs hold half the warps per SM and ran slower (64 x 4 and
-// 32 x 8: 12.4 and 15.5 G/s against 21.4 on the 1024 x 256 reactive gas,
-// 25.2 and 26.6 against 31.2 on 2048 x 1024).
-constexpr int tma_tile_x(int S) { return S <= 2 ? 64 : 32; }
-constexpr int tma_tile_y(int S) { return S == 1 ? 4 : S == 2 ? 8 : S == 3 ? 8 : 6; }
-constexpr int tma_cw(int S) { return S == 2 ? 2 : 1; }
+// species: 32 x 7 with one cell per thread (56 KB, four CTAs of 224
+// threads), and on large grids two cells per thread on PAIR_TX x PAIR_TY =
+// 64 x 8 cells (110 KB, two CTAs of 256 threads): one thread per cell runs
+// 812 instructions per species-cell and is issue-bound; pairs run 528, and
+// the taller tile keeps 16 warps per SM (on 4096 x 4096: 42.0 G/s against
+// 37.7; pairs on 64 x 4, 64 x 6 and 64 x 7 gave 39.6, 36.1 and 39.9).  With
+// fewer CTAs per wave the pair tile loses on small grids (KH, G/s, pairs
+// against one cell: 256^2 6.6 / 8.9, 512^2 17.6 / 21.8, 768^2 21.6 / 24.9,
+// 1024^2 26.6 / 28.7, 1536^2 33.7 / 32.9, 2048^2 37.8 / 35.1), so pairs run
+// from PAIR_MIN_TILES tiles up.  Three species in pairs hold half the warps
+// per SM and ran slower (64 x 4 and 32 x 8: 12.4 and 15.5 G/s against 21.4
+// on the 1024 x 256 reactive gas, 25.2 and 26.6 against 31.2 on 2048 x 1024).
+constexpr int tma_tile_x(int S) { return S == 1 ? 64 : 32; }
+constexpr int tma_tile_y(int S) { return S == 1 ? 4 : S == 2 ? 7 : S == 3 ? 8 : 6; }
+constexpr int PAIR_TX = 64, PAIR_TY = 8;
+constexpr long long PAIR_MIN_TILES = 4096;
 
 // CTAs of a TX x TY tile kernel that fit on one SM at once, limited by
 // shared memory (the tile plus halo of 16 S float planes, and 1 KB reserved

@@ -15,12 +15,20 @@ int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, v
 
 bool tma_supported(const dbm_params &p) { return p.precision == DBM_FP32 && p.nspecies <= 4; }
 
-static int tma_box(const dbm_params &p, unsigned box[3])
+// The tile of the TMA-staged step: two cells per thread for two species
+// when asked for, or (DBM_KERNEL_AUTO / DBM_KERNEL_TMA) on grids of at least
+// PAIR_MIN_TILES pair tiles; else the species count's one-cell tile.
+static void choose_tile(dbm_handle *h)
 {
-    box[0] = tma_tile_x(p.nspecies) + 8;
-    box[1] = tma_tile_y(p.nspecies) + 4;
-    box[2] = 16 * p.nspecies;
-    return 0;
+    const dbm_params &p = h->p;
+    bool pair = false;
+    if (p.nspecies == 2 && p.step_kernel != DBM_KERNEL_TMA_CELL) {
+        const long long tiles = (long long)((p.nx + PAIR_TX - 1) / PAIR_TX) * ((p.ny + PAIR_TY - 1) / PAIR_TY);
+        pair = p.step_kernel == DBM_KERNEL_TMA_PAIR || tiles >= PAIR_MIN_TILES;
+    }
+    h->tma_tx = pair ? PAIR_TX : tma_tile_x(p.nspecies);
+    h->tma_ty = pair ? PAIR_TY : tma_tile_y(p.nspecies);
+    h->tma_cw = pair ? 2 : 1;
 }
 
 typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -33,6 +41,7 @@ typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32
 int make_tensor_maps(dbm_handle *h)
 {
     h->tma_ok = 0;
+    h->tma_tx = h->tma_ty = h->tma_cw = 0;
     if (!tma_supported(h->p)) return DBM_OK;
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -45,15 +54,17 @@ int make_tensor_maps(dbm_handle *h)
     const dbm_layout &L = h->lay;
     cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)(16 * h->p.nspecies)};
     cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
-    cuuint32_t box[3], estr[3] = {1, 1, 1};
-    unsigned b[3];
-    tma_box(h->p, b);
-    for (int i = 0; i < 3; ++i) box[i] = b[i];
+    choose_tile(h);
+    cuuint32_t box[3] = {(cuuint32_t)(h->tma_tx + 8), (cuuint32_t)(h->tma_ty + 4), (cuuint32_t)(16 * h->p.nspecies)};
+    cuuint32_t estr[3] = {1, 1, 1};
     for (int k = 0; k < 2; ++k) {
         CUresult r = encode(&h->tmap[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->f[k], dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return DBM_OK;
+        if (r != CUDA_SUCCESS) {
+            h->tma_tx = h->tma_ty = h->tma_cw = 0;
+            return DBM_OK;
+        }
     }
     h->tma_ok = 1;
     return DBM_OK;
@@ -82,13 +93,15 @@ int launch_step(dbm_handle *h, int cur, cudaStream_t st)
     if (h->tma_ok && want != DBM_KERNEL_GENERIC) {
         const CUtensorMap *tm = &h->tmap[cur];
         switch (h->p.nspecies) {
-        case 1: return launch_step_tma_t<1, tma_tile_x(1), tma_tile_y(1), tma_cw(1)>(h, tm, fin, fout, st);
-        case 2: return launch_step_tma_t<2, tma_tile_x(2), tma_tile_y(2), tma_cw(2)>(h, tm, fin, fout, st);
-        case 3: return launch_step_tma_t<3, tma_tile_x(3), tma_tile_y(3), tma_cw(3)>(h, tm, fin, fout, st);
-        case 4: return launch_step_tma_t<4, tma_tile_x(4), tma_tile_y(4), tma_cw(4)>(h, tm, fin, fout, st);
+        case 1: return launch_step_tma_t<1, tma_tile_x(1), tma_tile_y(1), 1>(h, tm, fin, fout, st);
+        case 2:
+            if (h->tma_cw == 2) return launch_step_tma_t<2, PAIR_TX, PAIR_TY, 2>(h, tm, fin, fout, st);
+            return launch_step_tma_t<2, tma_tile_x(2), tma_tile_y(2), 1>(h, tm, fin, fout, st);
+        case 3: return launch_step_tma_t<3, tma_tile_x(3), tma_tile_y(3), 1>(h, tm, fin, fout, st);
+        case 4: return launch_step_tma_t<4, tma_tile_x(4), tma_tile_y(4), 1>(h, tm, fin, fout, st);
         }
     }
-    if (want == DBM_KERNEL_TMA) return DBM_ERR_INVALID;
+    if (want != DBM_KERNEL_AUTO && want != DBM_KERNEL_GENERIC) return DBM_ERR_INVALID;
     if (h->p.precision == DBM_BF16DEV) return launch_step_bf16(h, cur, st);
     if (h->p.precision == DBM_FP64) return launch_step_f64(h, cur, st);
     if (h->p.precision == DBM_FP32) return launch_generic(h, fin, fout, st);

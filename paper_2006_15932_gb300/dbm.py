@@ -34,11 +34,12 @@ ERRORS = {
     -7: "DBM_ERR_STABILITY",
     -8: "DBM_ERR_TIMEOUT",
 }
-KERNELS = {"auto": 0, "generic": 1, "tma": 2}
+KERNELS = {"auto": 0, "generic": 1, "tma": 2, "tma_cell": 3, "tma_pair": 4}
 EXPORTS = [
     "dbm_init", "dbm_init_error", "dbm_equilibrium_matrix", "dbm_get_layout", "dbm_state_bytes", "dbm_scratch_bytes",
     "dbm_bind", "dbm_set_state", "dbm_set_f", "dbm_get_f", "dbm_step", "dbm_moments",
     "dbm_nonequilibrium", "dbm_conservation", "dbm_conservation_noalloc", "dbm_status", "dbm_steps_taken",
+    "dbm_step_tile",
     "dbm_last_error", "dbm_destroy", "dbm_batch_table_bytes", "dbm_batch_create", "dbm_batch_tune",
     "dbm_batch_step", "dbm_batch_info", "dbm_batch_get_config", "dbm_batch_set_config", "dbm_batch_last_error",
     "dbm_batch_destroy",
@@ -128,6 +129,7 @@ def load(path: str = LIB_PATH):
     L.dbm_status.argtypes = [H, vp, C.POINTER(C.c_uint)]
     L.dbm_steps_taken.argtypes = [H]
     L.dbm_steps_taken.restype = C.c_longlong
+    L.dbm_step_tile.argtypes = [H] + [C.POINTER(C.c_int)] * 3
     L.dbm_last_error.argtypes = [H]
     L.dbm_last_error.restype = C.c_char_p
     L.dbm_destroy.argtypes = [H]
@@ -272,6 +274,14 @@ def dbm_steps_taken(h) -> int:
     return load().dbm_steps_taken(h)
 
 
+def dbm_step_tile(h) -> tuple[int, int, int]:
+    """(tile_x, tile_y, cells_per_thread) of the step's shared-memory tile;
+    (0, 0, 0) when the step runs a kernel without one."""
+    tx, ty, cw = C.c_int(), C.c_int(), C.c_int()
+    _check(h, load().dbm_step_tile(h, C.byref(tx), C.byref(ty), C.byref(cw)))
+    return tx.value, ty.value, cw.value
+
+
 def dbm_last_error(h) -> str:
     return load().dbm_last_error(h).decode()
 
@@ -394,6 +404,11 @@ class Solver:
 
     def status(self):
         return dbm_status(self.h, self._st())
+
+    def step_tile(self):
+        """(tile_x, tile_y, cells_per_thread) of the step kernel; zeros when
+        it has no shared-memory tile."""
+        return dbm_step_tile(self.h)
 
     def close(self):
         if self.h:

@@ -179,6 +179,23 @@ def _moment_matrix_from_velocities(sp):
     return M
 
 
+def test_step_kernel_choices(D):
+    """Unknown kernels, the two-cell step outside FP32 with two species and
+    a TMA kernel for BF16DEV are refused at init; the tile is known only
+    once buffers are bound."""
+    pb2, pb3 = W.random_smooth(8, 8, 2), W.random_smooth(8, 8, 3)
+    for pb, prec, kern in ((pb2, "fp32", 5), (pb2, "fp32", -1), (pb3, "fp32", "tma_pair"),
+                           (pb2, "fp64", "tma_pair"), (pb2, "bf16dev", "tma_cell")):
+        with pytest.raises(D.DbmError) as e:
+            D.dbm_init(D.params_from_problem(pb, prec, kern))
+        assert e.value.code == -1, (prec, kern)
+    h = D.dbm_init(D.params_from_problem(pb2, "fp32", "tma_pair"))
+    with pytest.raises(D.DbmError) as e:
+        D.dbm_step_tile(h)
+    assert e.value.code == -3
+    D.dbm_destroy(h)
+
+
 def test_bf16dev_scope(D):
     """BF16-deviation storage: up to 4 species, no reaction, no force."""
     pb = W.random_smooth(8, 8, 2)

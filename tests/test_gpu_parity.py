@@ -264,7 +264,8 @@ def test_fp32_two_species_against_oracle(D, orc, nx, ny, react):
     reaction and force on."""
     pb = _two_species(nx, ny, (W.OUTFLOW, W.PERIODIC), react, True)
     p, f0 = _noneq_f(orc, pb)
-    s = D.Solver(pb, "fp32")
+    s = D.Solver(pb, "fp32", step_kernel="tma_pair")
+    assert s.step_tile() == (64, 8, 2)
     s.set_f(f0)
     s.step(50)
     f = s.get_f().cpu().numpy()
@@ -294,13 +295,31 @@ def test_pair_kernel_matches_generic(D, orc, nx, ny, bc, react, force):
     pb = _two_species(nx, ny, bc, react, force)
     p, f0 = _noneq_f(orc, pb)
     out = {}
-    for kern in ("generic", "tma"):
+    for kern in ("generic", "tma_pair"):
         s = D.Solver(pb, "fp32", step_kernel=kern)
         s.set_f(f0)
         s.step(6)
         out[kern] = s.get_f().cpu().numpy()
         assert s.status()[0] == 0
-    assert np.array_equal(out["tma"], out["generic"])
+    assert np.array_equal(out["tma_pair"], out["generic"])
+
+
+def test_step_tile_choice(D):
+    """The handle's tile: two cells per thread for two species on grids of
+    at least 4096 tiles of 64 x 8 cells (or when asked for), else one cell
+    per thread; no tile for the generic, FP64 and BF16DEV steps."""
+    kh = W.kh_shear_layer(2048, ny=1024)
+    small = W.kh_shear_layer(1024)
+    cases = [(kh, "fp32", "auto", (64, 8, 2)), (kh, "fp32", "tma_cell", (32, 7, 1)),
+             (small, "fp32", "auto", (32, 7, 1)), (small, "fp32", "tma_pair", (64, 8, 2)),
+             (small, "fp32", "generic", (0, 0, 0)), (small, "fp64", "auto", (0, 0, 0)),
+             (small, "bf16dev", "auto", (0, 0, 0)),
+             (W.random_smooth(70, 23, 3), "fp32", "auto", (32, 8, 1)),
+             (W.random_smooth(70, 23, 1), "fp32", "tma", (64, 4, 1))]
+    for pb, prec, kern, want in cases:
+        s = D.Solver(pb, prec, step_kernel=kern)
+        assert s.step_tile() == want, (pb.name, prec, kern)
+        s.close()
 
 
 # ---------------------------------------------------------------------------
