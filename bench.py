@@ -128,7 +128,7 @@ def step_kernel_name(pb, precision, solver):
     if precision == "fp64":
         return f"k_step_f64<{pb.ns}>"
     if precision == "bf16dev":
-        return f"k_step_bf16<{pb.ns},32,16>"
+        return f"k_step_bf16<{pb.ns},32,16,2>"
     tx, ty, cw = solver.step_tile()
     if tx:
         return f"k_step_tma<{pb.ns},{tx},{ty},{cw}>"

@@ -15,7 +15,7 @@ namespace dbm {
 
 // CTAs of the BF16 step's TX x TY tile that fit on one SM (shared memory for
 // the rebuilt FP32 tile plus its radius-2 halo, at least 64 registers per
-// thread), at most four.
+// cell), at most four.
 constexpr int bf16_ctas_per_sm(int S, int TX, int TY)
 {
     const int by_smem = (227 * 1024) / ((TX + 4) * (TY + 4) * S * 64 + 1024);
@@ -24,8 +24,8 @@ constexpr int bf16_ctas_per_sm(int S, int TX, int TY)
     return n > 4 ? 4 : n < 1 ? 1 : n;
 }
 
-template <int S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, bf16_ctas_per_sm(S, TX, TY))
+template <int S, int TX, int TY, int CW>
+__global__ void __launch_bounds__(TX / CW * TY, bf16_ctas_per_sm(S, TX, TY))
     k_step_bf16(const __grid_constant__ StepConsts<float, S> c, BfState in, BfState out,
                 unsigned *__restrict__ flag)
 {
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(TX *TY, bf16_ctas_per_sm(S, TX, TY))
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tile = reinterpret_cast<float *>(smem_raw);  // [16 S][BY][BX], column 0 = x0 - 2
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int nthr = TX * TY, tid = ty * TX + tx;
+    const int nthr = TX / CW * TY, tid = ty * (TX / CW) + tx;
     const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
 
     // phase A: rebuild f for the tile and its halo; a halo cell outside the
@@ -59,15 +59,18 @@ __global__ void __launch_bounds__(TX *TY, bf16_ctas_per_sm(S, TX, TY))
     }
     __syncthreads();
 
-    // phase B: the step from shared memory
-    const int x = bx0 + tx, y = by0 + ty;
+    // phase B: the step from shared memory, CW adjacent cells per thread
+    const int x = bx0 + CW * tx, y = by0 + ty;
     if (x >= c.nx || y >= c.ny) return;
-    SmemTile t;
-    t.base = tile + (ty + 2) * BX + (tx + 2);
-    t.P = BY * BX;
-    t.py = BX;
+    const float *base = tile + (ty + 2) * BX + (CW * tx + 2);
     BfOut o{out, S};
-    step_cell<S>(c, c, t, x, y, true, o, flag);
+    if constexpr (CW == 2) {
+        const SmemTile2 t{base, BY * BX, BX};
+        step_cell<S>(c, c, t, x, y, x + 1 < c.nx, o, flag);
+    } else {
+        const SmemTile t{base, BY * BX, BX};
+        step_cell<S>(c, c, t, x, y, true, o, flag);
+    }
 }
 
 // State from macroscopic fields: reference moments n^s = rho^s/m^s, u, T
@@ -166,7 +169,9 @@ __global__ void __launch_bounds__(128)
 // launchers
 // ---------------------------------------------------------------------------
 
-constexpr int BF_TX = 32, BF_TY = 16;  // measured fastest of 64x8, 32x16, 32x8, 32x7 and 64x4
+// one cell per thread: 32 x 16 measured fastest of 64x8, 32x16, 32x8, 32x7
+// and 64x4; BF_CW = 2: two adjacent cells per thread (packed FP32x2 step)
+constexpr int BF_TX = 32, BF_TY = 16, BF_CW = 2;
 
 template <int S>
 static int step_bf16_t(dbm_handle *h, int cur, cudaStream_t st)
@@ -174,17 +179,18 @@ static int step_bf16_t(dbm_handle *h, int cur, cudaStream_t st)
     constexpr size_t smem = (size_t)(BF_TX + 4) * (BF_TY + 4) * S * Q * sizeof(float);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_bf16<S, BF_TX, BF_TY>,
+        cudaError_t e = cudaFuncSetAttribute(k_step_bf16<S, BF_TX, BF_TY, BF_CW>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return set_cuda_error(h, e, "BF16 step kernel shared-memory attribute");
         attr_set = true;
     }
     StepConsts<float, S> c;
     fill_step_consts<float, S>(h, c);
-    dim3 block(BF_TX, BF_TY);
+    dim3 block(BF_TX / BF_CW, BF_TY);
     dim3 grid((h->p.nx + BF_TX - 1) / BF_TX, (h->p.ny + BF_TY - 1) / BF_TY);
-    k_step_bf16<S, BF_TX, BF_TY><<<grid, block, smem, st>>>(c, bf_state(h, h->f[cur]), bf_state(h, h->f[cur ^ 1]),
-                                                            (unsigned *)h->scratch);
+    k_step_bf16<S, BF_TX, BF_TY, BF_CW><<<grid, block, smem, st>>>(c, bf_state(h, h->f[cur]),
+                                                                   bf_state(h, h->f[cur ^ 1]),
+                                                                   (unsigned *)h->scratch);
     return set_cuda_error(h, cudaGetLastError(), "BF16 step kernel launch");
 }
 

@@ -37,9 +37,11 @@ struct BfState {
 };
 
 // Output policy of the step: delta^{n+1} = f^{n+1} - f^eq(moments of f^n)
-// (the collision equilibrium the step has just built) and those moments.
-// No ghost cells: the step rebuilds a boundary tile's halo from the source
-// cells (periodic wrap or outflow edge).
+// (the collision equilibrium the step has just built) and those moments, for
+// one cell or for the pair (x, y), (x + 1, y) (x even: the pair's bfloat16
+// values are one 4-byte store, its floats one 8-byte store).  No ghost
+// cells: the step rebuilds a boundary tile's halo from the source cells
+// (periodic wrap or outflow edge).
 struct BfOut {
     static constexpr bool kNoImages = true;
     BfState st;
@@ -48,15 +50,37 @@ struct BfOut {
     {
         __stcs(st.d + (long long)p * st.P + w.cell, __float2bfloat16_rn(g - e));
     }
-    __device__ __forceinline__ void put_n(const Site &w, int s, float n) const
+    __device__ __forceinline__ void put(const Site &w, int p, float2 g, float2 e) const
     {
-        __stcs(st.mom + (long long)s * st.P + w.cell, n);
+        __nv_bfloat16 *q = st.d + (long long)p * st.P + w.cell;
+        if (w.two)
+            __stcs(reinterpret_cast<__nv_bfloat162 *>(q), __floats2bfloat162_rn(g.x - e.x, g.y - e.y));
+        else
+            __stcs(q, __float2bfloat16_rn(g.x - e.x));
     }
-    __device__ __forceinline__ void put_mix(const Site &w, float ux, float uy, float T) const
+    __device__ __forceinline__ void put_f(const Site &w, long long plane, float v) const
     {
-        __stcs(st.mom + (long long)S * st.P + w.cell, ux);
-        __stcs(st.mom + (long long)(S + 1) * st.P + w.cell, uy);
-        __stcs(st.mom + (long long)(S + 2) * st.P + w.cell, T);
+        __stcs(st.mom + plane * st.P + w.cell, v);
+    }
+    __device__ __forceinline__ void put_f(const Site &w, long long plane, float2 v) const
+    {
+        float *q = st.mom + plane * st.P + w.cell;
+        if (w.two)
+            __stcs(reinterpret_cast<float2 *>(q), v);
+        else
+            __stcs(q, v.x);
+    }
+    template <class V>
+    __device__ __forceinline__ void put_n(const Site &w, int s, V n) const
+    {
+        put_f(w, s, n);
+    }
+    template <class V>
+    __device__ __forceinline__ void put_mix(const Site &w, V ux, V uy, V T) const
+    {
+        put_f(w, S, ux);
+        put_f(w, S + 1, uy);
+        put_f(w, S + 2, T);
     }
     __device__ __forceinline__ void images(const Site &, int) const {}
     __device__ __forceinline__ void images_mix(const Site &) const {}
