@@ -36,9 +36,11 @@ __global__ void __launch_bounds__(TX / CW * TY, bf16_ctas_per_sm(S, TX, TY))
     const int nthr = TX / CW * TY, tid = ty * (TX / CW) + tx;
     const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
 
-    // phase A: rebuild f for the tile and its halo; a halo cell outside the
-    // domain is rebuilt from its source cell (periodic wrap, or the edge cell
-    // for outflow), so the stored ghost cells are neither read nor written
+    // phase A: rebuild f for the tile and its halo, one cell per iteration
+    // (two cells per iteration in packed FP32x2 measured slower: 18.7
+    // against 23.8 G/s on KH 4096^2); a halo cell outside the domain is
+    // rebuilt from its source cell (periodic wrap, or the edge cell for
+    // outflow), so the stored ghost cells are neither read nor written
     for (int k = tid; k < BX * BY; k += nthr) {
         const int rr = k / BX, cc = k % BX;
         const int x = bx0 - 2 + cc, y = by0 - 2 + rr;

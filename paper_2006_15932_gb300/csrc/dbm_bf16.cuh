@@ -17,16 +17,16 @@
 
 namespace dbm {
 
-// Reference equilibrium of species s at stored (n, u, T), FP32.
-template <int S>
-__device__ __forceinline__ void feq_ref(const StepConsts<float, S> &k, int s, float n, float ux, float uy,
-                                        float T, float f[Q])
+// Reference equilibrium of species s at stored (n, u, T), FP32, for one
+// cell (V = float) or two (V = float2, bit for bit the same per cell).
+template <int S, class V>
+__device__ __forceinline__ void feq_ref(const StepConsts<float, S> &k, int s, V n, V ux, V uy, V T, V f[Q])
 {
-    float c[16], o[16];
-    fhat_blocks<float>(n, ux, uy, T * k.inv_m[s], k.dpi[s], c);
-    solve_blocks<float>(k, s, c, o);
+    V c[16], o[16];
+    fhat_blocks<V>(n, ux, uy, vmul(T, bc<V>(k.inv_m[s])), k.dpi[s], c);
+    solve_blocks<V>(k, s, c, o);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) f[i] = feq_of<float>(i, o);
+    for (int i = 0; i < Q; ++i) f[i] = feq_of<V>(i, o);
 }
 
 // Pointers of one BF16-deviation state buffer.
