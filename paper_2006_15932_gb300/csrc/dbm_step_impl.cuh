@@ -71,9 +71,10 @@ __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ float vmm(float a, float b) { return minmod(a, b); }
 
-// The packed operations are written as PTX with an explicit .rn rounding:
-// like the scalar _rn intrinsics, such an add or multiply is never fused
-// into an FMA by the compiler.
+// The packed operations are written as PTX with an explicit .rn rounding,
+// which keeps the front end from contracting them; the backend can still
+// fuse a packed multiply into a following packed add (see above), which the
+// step avoids by never passing a product to an add or a subtract.
 __device__ __forceinline__ unsigned long long vpk(float2 a)
 {
     unsigned long long r;
