@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -179,7 +180,8 @@ class ClockSampler:
 
     def start(self):
         try:
-            out_dir = os.path.join(ROOT, "gpurun_out")
+            # raw samples (the JSON line carries their summary)
+            out_dir = os.environ.get("DBM_CLOCKS_DIR") or tempfile.gettempdir()
             os.makedirs(out_dir, exist_ok=True)
             self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
             self.fh = open(self.path, "w")
