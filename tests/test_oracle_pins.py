@@ -574,3 +574,106 @@ def test_shear_wave_viscosity(orc):
     nu = rate / k ** 2
     print("measured nu", nu, "Chapman-Enskog", tau * T / m)
     assert nu == pytest.approx(tau * T / m, rel=0.01)  # measured: 0.03 %
+
+
+# ---------------------------------------------------------------------------
+# Outputs: macroscopic fields and the nonequilibrium moments (Eqs. Delta2,
+# Delta31, Delta3, Delta42 and the energy diagnostics that follow them)
+# ---------------------------------------------------------------------------
+
+def _equilibrium_state(orc, ns=3, nx=9, ny=7, seed=4):
+    pb = W.random_smooth(nx, ny, ns, seed=seed)
+    p = W.to_oracle_params(pb)
+    return pb, p, orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
+
+
+def _rel(a, b, scale):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / scale)
+
+
+def test_moments_of_the_equilibrium_are_its_fields(orc):
+    """f^eq built from (rho^s, u, T) has exactly those moments: n^s =
+    rho^s / m^s, u^s = u and T^s = T for every species, and the mixture
+    rho = sum rho^s, u, T and p = n T."""
+    pb, p, f = _equilibrium_state(orc)
+    mom = orc.moments(p, f)
+    S = pb.ns
+    m = np.array([sp.m for sp in pb.species])[:, None, None]
+    n = pb.rho_s / m
+    uscale = max(np.max(np.abs(pb.ux)), np.max(np.abs(pb.uy)))
+    for s in range(S):
+        assert _rel(mom[4 * s], n[s], np.max(n[s])) < 1e-12
+        assert _rel(mom[4 * s + 1], pb.ux, uscale) < 1e-12
+        assert _rel(mom[4 * s + 2], pb.uy, uscale) < 1e-12
+        assert _rel(mom[4 * s + 3], pb.T, np.max(pb.T)) < 1e-12
+    rho = pb.rho_s.sum(axis=0)
+    assert _rel(mom[4 * S], rho, np.max(rho)) < 1e-12
+    assert _rel(mom[4 * S + 1], pb.ux, uscale) < 1e-12
+    assert _rel(mom[4 * S + 2], pb.uy, uscale) < 1e-12
+    assert _rel(mom[4 * S + 3], pb.T, np.max(pb.T)) < 1e-12
+    pr = n.sum(axis=0) * pb.T
+    assert _rel(mom[4 * S + 4], pr, np.max(pr)) < 1e-12
+
+
+def test_nonequilibrium_moments_vanish_at_equilibrium(orc):
+    """For f = f^eq every Delta is zero, M(f) equals M(f^eq), and the
+    equilibrium diagnostics take their closed forms (D = 2):
+    M_2aa(f^eq)/2 = (n T + rho u_a^2)/2 and
+    M_3,1a(f^eq)/2 = rho u_a ((D + I + 2) T/m + u.u)/2."""
+    pb, p, f = _equilibrium_state(orc)
+    d = orc.nonequilibrium(p, f)
+    u2 = pb.ux ** 2 + pb.uy ** 2
+    for s, sp in enumerate(pb.species):
+        rows = d[20 * s:20 * s + 20]
+        scale = np.max(np.abs(rows[12:20]))
+        assert np.max(np.abs(rows[0:12])) / scale < 1e-12
+        assert _rel(rows[12:14], rows[14:16], scale) < 1e-13
+        assert _rel(rows[16:18], rows[18:20], scale) < 1e-13
+        rho = pb.rho_s[s]
+        n = rho / sp.m
+        assert _rel(rows[14], 0.5 * (n * pb.T + rho * pb.ux ** 2), scale) < 1e-12
+        assert _rel(rows[15], 0.5 * (n * pb.T + rho * pb.uy ** 2), scale) < 1e-12
+        a2 = (2.0 + sp.I + 2.0) * pb.T / sp.m + u2
+        assert _rel(rows[18], 0.5 * rho * pb.ux * a2, scale) < 1e-12
+        assert _rel(rows[19], 0.5 * rho * pb.uy * a2, scale) < 1e-12
+
+
+def _permutation(vx, vy, eta, image):
+    """Index map i -> j of the velocity set with (vx_j, vy_j) = image(vx_i,
+    vy_i) and the same internal speed."""
+    perm = []
+    for i in range(len(vx)):
+        tx, ty = image(vx[i], vy[i])
+        j = [k for k in range(len(vx))
+             if abs(vx[k] - tx) < 1e-12 and abs(vy[k] - ty) < 1e-12 and eta[k] == eta[i]]
+        assert len(j) == 1
+        perm.append(j[0])
+    return perm
+
+
+def test_nonequilibrium_moments_follow_the_square_symmetries(orc):
+    """Mirroring a nonequilibrium state in x (v_x -> -v_x) flips exactly the
+    components odd in x; exchanging x and y exchanges the x and y
+    components.  A wrong index or sign in any of the 20 sums fails one of
+    the two."""
+    pb, p, feq = _equilibrium_state(orc, ns=2, nx=5, ny=3, seed=8)
+    rng = np.random.default_rng(9)
+    f = feq * (1.0 + 0.1 * rng.uniform(-1, 1, size=feq.shape))
+    d = orc.nonequilibrium(p, f)
+    mirror_sign = np.array([1, -1, 1, -1, 1, -1, 1, -1, 1, 1, -1, 1, 1, 1, 1, 1, -1, 1, -1, 1])
+    swap_rows = [2, 1, 0, 4, 3, 8, 7, 6, 5, 11, 10, 9, 13, 12, 15, 14, 17, 16, 19, 18]
+    fm, fs = np.empty_like(f), np.empty_like(f)
+    for s, sp in enumerate(pb.species):
+        vx, vy, eta = orc.velocities(sp)
+        pm = _permutation(vx, vy, eta, lambda x, y: (-x, y))
+        ps = _permutation(vx, vy, eta, lambda x, y: (y, x))
+        fm[s] = f[s][pm]
+        fs[s] = f[s][ps]
+    dm = orc.nonequilibrium(p, fm)
+    ds = orc.nonequilibrium(p, fs)
+    for s in range(pb.ns):
+        rows = d[20 * s:20 * s + 20]
+        scale = np.max(np.abs(rows))
+        assert np.max(np.abs(rows[0:12])) / scale > 1e-4  # a real departure
+        assert _rel(dm[20 * s:20 * s + 20], mirror_sign[:, None, None] * rows, scale) < 1e-12
+        assert _rel(ds[20 * s:20 * s + 20], rows[swap_rows], scale) < 1e-12
