@@ -677,3 +677,27 @@ def test_nonequilibrium_moments_follow_the_square_symmetries(orc):
         assert np.max(np.abs(rows[0:12])) / scale > 1e-4  # a real departure
         assert _rel(dm[20 * s:20 * s + 20], mirror_sign[:, None, None] * rows, scale) < 1e-12
         assert _rel(ds[20 * s:20 * s + 20], rows[swap_rows], scale) < 1e-12
+
+
+def test_conserved_totals_of_the_equilibrium(orc):
+    """The conserved totals of f^eq(rho^s, u, T) in closed form: species
+    masses sum rho^s, momentum sum rho u, energy sum over species and cells
+    of n^s (D + I^s) T / 2 + rho^s u.u / 2 (D = 2), and with a reaction the
+    heat still bound in the fuel, Q n^fuel / |a^fuel| summed over cells."""
+    pb = W.random_smooth(9, 7, 3, seed=5, reactive=True)
+    p = W.to_oracle_params(pb)
+    f = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
+    c = orc.conservation(p, f)
+    S = pb.ns
+    rho = pb.rho_s.sum(axis=0)
+    u2 = pb.ux ** 2 + pb.uy ** 2
+    want = [pb.rho_s[s].sum() for s in range(S)]
+    want += [(rho * pb.ux).sum(), (rho * pb.uy).sum()]
+    energy = sum(((pb.rho_s[s] / sp.m) * (2.0 + sp.I) * pb.T / 2 + pb.rho_s[s] * u2 / 2).sum()
+                 for s, sp in enumerate(pb.species))
+    fuel = pb.species[pb.fuel]
+    bound = (pb.Q * (pb.rho_s[pb.fuel] / fuel.m) / abs(fuel.a)).sum()
+    want += [energy, bound]
+    want = np.array(want)
+    scale = np.maximum(np.abs(want), np.max(np.abs(want[:S])))
+    assert np.max(np.abs(c - want) / scale) < 1e-12, (c, want)
