@@ -701,3 +701,21 @@ def test_conserved_totals_of_the_equilibrium(orc):
     want = np.array(want)
     scale = np.maximum(np.abs(want), np.max(np.abs(want[:S])))
     assert np.max(np.abs(c - want) / scale) < 1e-12, (c, want)
+
+
+@pytest.mark.parametrize("bc", [(W.PERIODIC, W.PERIODIC), (W.OUTFLOW, W.PERIODIC), (W.PERIODIC, W.OUTFLOW)])
+def test_step_region_is_a_window_of_the_full_step(orc, bc):
+    """The windowed step (the reference of the sampled full-size GPU checks)
+    equals the same window of one full-grid step, bit for bit, for windows
+    touching every edge and one in the interior, with reaction and force."""
+    pb = W.random_smooth(13, 11, 3, seed=7, reactive=True, force=True, bc=bc)
+    p = W.to_oracle_params(pb)
+    rng = np.random.default_rng(2)
+    f0 = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
+    f0 = f0 * (1.0 + 0.05 * rng.uniform(-1, 1, size=f0.shape))
+    full, st = orc.run(p, f0, 1)
+    assert st == 0
+    for (x0, x1, y0, y1) in [(0, 5, 0, 4), (8, 13, 7, 11), (0, 13, 5, 6), (4, 9, 3, 8), (12, 13, 0, 11)]:
+        got, st = orc.step_region(p, f0, x0, x1, y0, y1)
+        assert st == 0
+        assert np.array_equal(got, full[:, :, y0:y1, x0:x1]), (x0, x1, y0, y1)
