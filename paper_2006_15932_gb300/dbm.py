@@ -165,6 +165,10 @@ def make_params(nx, ny, species, *, dx, dy, dt, bc_x=PERIODIC, bc_y=PERIODIC, fu
     p.fuel, p.oxidizer = int(fuel), int(oxid)
     p.k_ov, p.Ea_over_R, p.Q = float(k_ov), float(Ea_over_R), float(Q)
     p.accel[0], p.accel[1] = float(accel[0]), float(accel[1])
+    if isinstance(precision, str) and precision not in PRECISIONS:
+        raise ValueError(f"precision {precision!r}: one of {sorted(PRECISIONS)}")
+    if isinstance(step_kernel, str) and step_kernel not in KERNELS:
+        raise ValueError(f"step_kernel {step_kernel!r}: one of {sorted(KERNELS)}")
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.step_kernel = KERNELS[step_kernel] if isinstance(step_kernel, str) else int(step_kernel)
     for s, sp in enumerate(species):

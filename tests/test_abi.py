@@ -194,6 +194,10 @@ def test_step_kernel_choices(D):
         D.dbm_step_tile(h)
     assert e.value.code == -3
     D.dbm_destroy(h)
+    with pytest.raises(ValueError):
+        D.params_from_problem(pb2, "fp32", "tma_quad")
+    with pytest.raises(ValueError):
+        D.params_from_problem(pb2, "fp16")
 
 
 def test_bf16dev_scope(D):
