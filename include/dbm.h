@@ -167,7 +167,10 @@ int dbm_scratch_bytes(const dbm_handle *h, size_t *bytes);
 
 /* Bind caller-owned device buffers: f_a and f_b of dbm_state_bytes each
  * (256-byte aligned), scratch of dbm_scratch_bytes.  f_a becomes the current
- * state.  The buffers must outlive every call that uses them. */
+ * state.  The buffers must outlive every call that uses them.  Builds the
+ * TMA descriptors of the two buffers and fixes the step's tile
+ * (dbm_step_tile); DBM_ERR_INVALID when dbm_params.step_kernel asks for a
+ * TMA-staged kernel that cannot run (not FP32, S > 4, no descriptor). */
 int dbm_bind(dbm_handle *h, void *f_a, void *f_b, void *scratch);
 
 /* f = f^eq(n^s = rho^s / m^s, u, T) in every cell from the macroscopic
