@@ -239,7 +239,7 @@ def cpu_baseline(pb_full, precision, seconds):
                    accel=pb_full.accel, rho_s=pb_full.rho_s[:, y0:y0 + ny, x0:x0 + nx],
                    ux=pb_full.ux[y0:y0 + ny, x0:x0 + nx], uy=pb_full.uy[y0:y0 + ny, x0:x0 + nx],
                    T=pb_full.T[y0:y0 + ny, x0:x0 + nx])
-    p = W.to_oracle_params(pb)
+    p = O.params_of(pb)
     f = O.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
     O.run(p, f, 1)  # start the OpenMP thread pool
     t0 = time.perf_counter()

@@ -114,6 +114,18 @@ class Params:
         return p
 
 
+def params_of(problem) -> Params:
+    """The oracle's parameter record for a problem description: any object
+    with the attributes nx, ny, species (each with m, I, tau, v, eta, a), dx,
+    dy, dt, bc_x, bc_y, fuel, oxid, k_ov, Ea_over_R, Q and accel, such as the
+    seeded workloads of the test inputs.  Reads attributes only."""
+    pb = problem
+    sp = [Species(m=s.m, I=s.I, tau=s.tau, v=tuple(s.v), eta=tuple(s.eta), a=s.a) for s in pb.species]
+    return Params(nx=pb.nx, ny=pb.ny, species=sp, dx=pb.dx, dy=pb.dy, dt=pb.dt, bc_x=pb.bc_x,
+                  bc_y=pb.bc_y, fuel=pb.fuel, oxid=pb.oxid, k_ov=pb.k_ov, Ea_over_R=pb.Ea_over_R,
+                  Q=pb.Q, accel=tuple(pb.accel))
+
+
 _lib = None
 
 

@@ -77,16 +77,6 @@ class Problem:
         return self.nx * self.ny
 
 
-def to_oracle_params(pb: Problem):
-    """The oracle's parameter record for a problem (test side only)."""
-    from oracle import oracle as O
-
-    sp = [O.Species(m=s.m, I=s.I, tau=s.tau, v=tuple(s.v), eta=tuple(s.eta), a=s.a) for s in pb.species]
-    return O.Params(nx=pb.nx, ny=pb.ny, species=sp, dx=pb.dx, dy=pb.dy, dt=pb.dt, bc_x=pb.bc_x,
-                    bc_y=pb.bc_y, fuel=pb.fuel, oxid=pb.oxid, k_ov=pb.k_ov, Ea_over_R=pb.Ea_over_R,
-                    Q=pb.Q, accel=tuple(pb.accel))
-
-
 # ---------------------------------------------------------------------------
 # configurations
 # ---------------------------------------------------------------------------

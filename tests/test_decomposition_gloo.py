@@ -32,10 +32,11 @@ def _free_port():
 
 def _problem(bc_y):
     sys.path.insert(0, ROOT)
+    from oracle import oracle as O
     from paper_2006_15932_gb300 import workloads as W
 
     pb = W.random_smooth(20, 18, 3, seed=41, reactive=True, force=True, bc=(W.OUTFLOW, bc_y))
-    return pb, W.to_oracle_params(pb)
+    return pb, O.params_of(pb)
 
 
 def _slabs(ny, world):

@@ -80,7 +80,7 @@ def test_batch_against_oracle(D, orc):
     batch.step(30)
     torch.cuda.synchronize()
     for pb, s in zip(pbs, sols):
-        p = W.to_oracle_params(pb)
+        p = orc.params_of(pb)
         f0 = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
         fr, st = orc.run(p, f0, 30)
         assert st == 0
@@ -210,7 +210,7 @@ def test_batched_workload_full_size_sampled(D, orc):
         pb = pbs[k]
         assert sols[k].status()[0] == 0
         f2 = sols[k].get_f().cpu().numpy()
-        p = W.to_oracle_params(pb)
+        p = orc.params_of(pb)
         w = 16
         corners = [(0, 0), (pb.nx - w, pb.ny - w),
                    (int(rng.integers(0, pb.nx - w)), int(rng.integers(0, pb.ny - w)))]

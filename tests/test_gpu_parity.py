@@ -57,7 +57,7 @@ def D():
 
 
 def _oracle_f0(orc, pb):
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     return p, orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
 
 
@@ -344,7 +344,7 @@ def test_full_size_one_step_sampled(D, orc, which):
     s.step(1)
     f1 = s.get_f()
     assert s.status()[0] == 0
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     f0n = f0.cpu().numpy()
     f1n = f1.cpu().numpy()
     del f0, f1

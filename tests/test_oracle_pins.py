@@ -409,7 +409,7 @@ def test_uniform_equilibrium_is_invariant(orc):
     sps = [W.species(m=1.0, tau=2e-5), W.species(m=2.0, I=2.0, tau=3e-5)]
     for bc in ((W.PERIODIC, W.PERIODIC), (W.OUTFLOW, W.PERIODIC), (W.OUTFLOW, W.OUTFLOW)):
         pb = W.uniform(9, 7, sps, rho_s=[0.4, 0.7], ux=0.13, uy=-0.08, T=0.95, bc_x=bc[0], bc_y=bc[1])
-        p = W.to_oracle_params(pb)
+        p = orc.params_of(pb)
         f0 = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
         f, st = orc.run(p, f0, 20)
         assert st == 0
@@ -418,7 +418,7 @@ def test_uniform_equilibrium_is_invariant(orc):
 
 def test_mass_and_momentum_conserved_on_periodic_grid(orc):
     pb = W.random_smooth(12, 10, 3, seed=3, unequal=True)
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     f0 = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
     c0 = orc.conservation(p, f0)
     f, st = orc.run(p, f0, 25)
@@ -442,7 +442,7 @@ def test_free_fall_velocity_is_a_t(orc):
     sps = [W.species(m=1.0, tau=2e-5), W.species(m=2.0, I=2.0, tau=3e-5)]
     a = -9.8
     pb = W.uniform(3, 3, sps, rho_s=[0.4, 0.9], T=1.0, accel=(0.0, a))
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     f0 = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
     f, st = orc.run(p, f0, 100)
     assert st == 0
@@ -462,7 +462,7 @@ def test_reactive_uniform_box_budget(orc):
     sps = [W.species(tau=2e-5, a=-1.0), W.species(tau=2e-5, a=-1.0), W.species(tau=2e-5, a=2.0)]
     pb = W.uniform(2, 2, sps, rho_s=[0.45, 0.45, 0.1], T=1.3, fuel=0, oxid=1, k_ov=50.0,
                    Ea_over_R=2.0, Q=0.8)
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     f = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
     c0 = orc.conservation(p, f)
     for _ in range(5):
@@ -486,7 +486,7 @@ def test_reactive_uniform_box_budget(orc):
 def test_status_flags_bad_input(orc):
     sps = [W.species(), W.species()]
     pb = W.uniform(4, 1, sps, rho_s=[0.5, 0.5], T=1.0)
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     f = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
     f[0, :, 0, 2] = -f[0, :, 0, 2]
     _, st = orc.run(p, f, 1)
@@ -522,7 +522,7 @@ def test_paper_shock_states_satisfy_rankine_hugoniot():
 @pytest.mark.slow
 def test_sod_shock_tube_against_exact_riemann(orc):
     pb = W.sod_tube(400, 2000)
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     f0 = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
     f, st = orc.run(p, f0, pb.nsteps)
     assert st == 0
@@ -558,7 +558,7 @@ def test_shear_wave_viscosity(orc):
     pb = W.Problem(name="shear", nx=nx, ny=1, species=sp, dx=dx, dy=dx, dt=dt,
                    rho_s=np.ones((1, 1, nx)), ux=np.zeros((1, nx)),
                    uy=(U * np.sin(k * x))[None, :], T=np.full((1, nx), T))
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     f = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
     amps, times = [], []
     nsteps = int(round(0.4 / (2 * math.pi) ** 2 / (tau * T / m) / dt))
@@ -583,7 +583,7 @@ def test_shear_wave_viscosity(orc):
 
 def _equilibrium_state(orc, ns=3, nx=9, ny=7, seed=4):
     pb = W.random_smooth(nx, ny, ns, seed=seed)
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     return pb, p, orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
 
 
@@ -685,7 +685,7 @@ def test_conserved_totals_of_the_equilibrium(orc):
     of n^s (D + I^s) T / 2 + rho^s u.u / 2 (D = 2), and with a reaction the
     heat still bound in the fuel, Q n^fuel / |a^fuel| summed over cells."""
     pb = W.random_smooth(9, 7, 3, seed=5, reactive=True)
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     f = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
     c = orc.conservation(p, f)
     S = pb.ns
@@ -709,7 +709,7 @@ def test_step_region_is_a_window_of_the_full_step(orc, bc):
     equals the same window of one full-grid step, bit for bit, for windows
     touching every edge and one in the interior, with reaction and force."""
     pb = W.random_smooth(13, 11, 3, seed=7, reactive=True, force=True, bc=bc)
-    p = W.to_oracle_params(pb)
+    p = orc.params_of(pb)
     rng = np.random.default_rng(2)
     f0 = orc.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
     f0 = f0 * (1.0 + 0.05 * rng.uniform(-1, 1, size=f0.shape))
