@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -285,11 +287,84 @@ def run_reference(args):
     return 0
 
 
+def serve_study(D, dev, mix, load, qmax, subset_n):
+    """Continuous batching on a request mix, measured three ways.
+
+    1. capacity: the mix arriving all at once, served (species-cell updates
+       per second over the makespan);
+    2. the served run: Poisson arrivals at `load` x capacity; p50 / p99
+       latency (arrival -> conserved totals on the host) and throughput;
+    3. the baseline, on a stated subset (the `subset_n` requests with the
+       fewest updates, all arriving at once): the same requests served with
+       continuous batching (FP32), solved one at a time in FP64 and in FP32
+       (real solves, serve.run_sequential); throughputs, latencies, and the
+       served results' largest relative L-inf distance from the FP64 solves
+       (the accuracy at which the throughputs are compared)."""
+    import dataclasses
+
+    import torch
+
+    from paper_2006_15932_gb300 import serve as SV
+    from paper_2006_15932_gb300 import workloads as W
+
+    SV.Server(device=dev, qmax=qmax).run(mix[:4])  # warm-up: kernels, allocator
+    cap = SV.summarize(SV.Server(device=dev, qmax=qmax).run(mix))["throughput"]
+    mean_units = sum(q.units for q in mix) / len(mix)
+    rate = load * cap / mean_units
+    timed = W.poisson_arrivals(mix, rate)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    srv = SV.Server(device=dev, qmax=qmax)
+    res = srv.run(timed)
+    clk = clocks.stop()
+    if any(r.status for r in res):
+        raise SystemExit("health flag raised while serving")
+    summ = SV.summarize(res)
+
+    sub = [dataclasses.replace(q, arrival=0.0) for q in sorted(mix, key=lambda q: q.units)[:subset_n]]
+    served = {r.rid: r for r in SV.Server(device=dev, qmax=qmax, keep_f=True).run(sub)}
+    seq64 = {r.rid: r for r in SV.run_sequential(sub, "fp64", device=dev, keep_f=True)}
+    seq32 = {r.rid: r for r in SV.run_sequential(sub, "fp32", device=dev)}
+    if any(r.status for r in list(served.values()) + list(seq64.values()) + list(seq32.values())):
+        raise SystemExit("health flag raised in the serving baseline")
+    acc = max(float(np.max(np.abs(served[k].f - seq64[k].f)) / np.max(np.abs(seq64[k].f))) for k in served)
+
+    def brief(results):
+        d = SV.summarize(list(results))
+        return {k: d[k] for k in ("p50_s", "p99_s", "mean_s", "makespan_s", "throughput")}
+
+    return {
+        "capacity_units_per_s": cap, "arrival_rate_per_s": rate, "load": load, "requests": len(mix),
+        "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "mean_s": summ["mean_s"],
+        "makespan_s": summ["makespan_s"], "throughput": summ["throughput"], "units": summ["units"],
+        "hbm_budget_bytes": srv.adm.budget, "admitted_peak_bytes": srv.adm.peak,
+        "batch_rebuilds": sum(g.rebuilds for g in srv.groups.values()), "quanta": srv.launch_quanta,
+        "batch_config": {k: (list(v) if isinstance(v, tuple) else v) for k, v in srv.config.items()},
+        "clocks": clk,
+        "baseline": {
+            "subset": f"the {len(sub)} requests of the mix with the fewest updates, all arriving at t = 0",
+            "units": sum(q.units for q in sub),
+            "served_fp32": brief(served.values()),
+            "sequential_fp64": brief(seq64.values()),
+            "sequential_fp32": brief(seq32.values()),
+            "served_vs_fp64_rel_linf_f": acc,
+            "how": "sequential = first come, first served, one request at a time, each a plain single-problem "
+                   "solve (real runs, serve.run_sequential)",
+        },
+    }
+
+
 def run_serve(args, D, dev):
-    """Serving: Poisson arrivals of the request mix at a fraction of the
-    measured capacity, continuous batching; p50/p99 latency and throughput,
-    against first-come-first-served sequential solves (FP64 and unbatched
-    FP32) whose service times come from throughputs measured here."""
+    """Serving (the request-mix configuration): Poisson arrivals at a
+    fraction of the measured capacity, continuous batching; p50/p99 latency
+    and throughput; sequential FP64 and FP32 solves of a stated subset of the
+    mix as the measured baseline, and of the whole mix as an extrapolation
+    from rates measured here."""
     import torch
 
     from paper_2006_15932_gb300 import serve as SV
@@ -298,92 +373,75 @@ def run_serve(args, D, dev):
     s_lo, s_hi = (int(v) for v in args.serve_sides.split(","))
     n_lo, n_hi = (int(v) for v in args.serve_steps.split(","))
     specs = W.serving_requests(args.serve_requests, lo=s_lo, hi=s_hi, steps=(n_lo, n_hi))
-    # capacity: the same mix (other seed, 1/20 of the steps) all arriving at once
-    cal = W.serving_requests(32, seed=W.SEED + 1, lo=s_lo, hi=s_hi,
-                             steps=(max(1, n_lo // 20), max(2, n_hi // 20)))
-    SV.Server(device=dev, qmax=args.serve_qmax).run(cal[:4])  # warm-up: kernels, allocator
-    cap = SV.summarize(SV.Server(device=dev, qmax=args.serve_qmax).run(cal))["throughput"]
-    mean_units = sum(s.units for s in specs) / len(specs)
-    rate = args.serve_load * cap / mean_units
-    specs = W.poisson_arrivals(specs, rate)
+    st = serve_study(D, dev, specs, args.serve_load, args.serve_qmax, subset_n=8)
 
-    uuid = None
-    try:
-        uuid = str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
-    clocks = ClockSampler(uuid)
-    clocks.start()
-    srv = SV.Server(device=dev, qmax=args.serve_qmax)
-    res = srv.run(specs)
-    clk = clocks.stop()
-    if any(r.status for r in res):
-        raise SystemExit("health flag raised while serving")
-    summ = SV.summarize(res)
-
-    # sequential references: FP64 and unbatched FP32 throughput per species
-    # count on a 512 x 512 shock tube (FP64 is ALU-bound, so its rate hardly
-    # depends on the size)
+    # extrapolation to the whole mix: FIFO queue with service times from the
+    # FP64 and unbatched FP32 rates measured per species count on a 512 x 512
+    # shock tube (FP64 is ALU-bound, so its rate hardly depends on the size)
     def rate_of(precision, ns, steps):
         spec = W.RequestSpec(rid=0, kind="shock", L=512, ns=ns, seed=1, nsteps=steps)
-        st = torch.cuda.Stream(device=dev)
-        with torch.cuda.stream(st):
+        stream = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(stream):
             s = D.Solver(W.request_problem(spec), precision, device=dev)
             s.set_state(*W.request_fields(spec, dev))
             s.step(2)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
+            e0.record(stream)
             s.step(steps)
-            e1.record(st)
-        st.synchronize()
+            e1.record(stream)
+        stream.synchronize()
         ms = e0.elapsed_time(e1)
         s.close()
         return 512 * 512 * ns * steps / (ms * 1e-3)
 
-    nss = sorted({s.ns for s in specs})
+    nss = sorted({q.ns for q in specs})
     r64 = {ns: rate_of("fp64", ns, 4) for ns in nss}
     r32 = {ns: rate_of("fp32", ns, 200) for ns in nss}
-    seq64 = SV.simulate_sequential(specs, r64)
-    seq32 = SV.simulate_sequential(specs, r32)
+    timed = W.poisson_arrivals(specs, st["arrival_rate_per_s"])
     peak, peak_kind = measured_peaks()
     bpu = BYTES_PER_UPDATE["fp32"]
     cfg = {"workload": "serve_poisson_request_mix", "requests": len(specs), "sides": [s_lo, s_hi],
            "side_distribution": "log-uniform", "species": nss, "reactive_fraction": 0.5,
-           "steps": [n_lo, n_hi], "precision": "fp32", "arrival_rate_per_s": rate,
-           "load": args.serve_load, "capacity_units_per_s": cap, "qmax": args.serve_qmax,
-           "batch_config": {k: (list(v) if isinstance(v, tuple) else v) for k, v in srv.config.items()},
-           "l2_policy": "inputs larger than L2"}
-    line = {"metric": METRIC, "value": summ["throughput"], "unit": UNIT, "n_gpus": 1, "steps": len(specs),
-            "warmup": 4, "ms_per_step": 1e3 * summ["makespan_s"] / len(specs), "higher_is_better": True,
+           "steps": [n_lo, n_hi], "precision": "fp32", "arrival_rate_per_s": st["arrival_rate_per_s"],
+           "load": args.serve_load, "capacity_units_per_s": st["capacity_units_per_s"], "qmax": args.serve_qmax,
+           "batch_config": st["batch_config"], "l2_policy": "inputs larger than L2"}
+    clk = st.pop("clocks")
+    line = {"metric": METRIC, "value": st["throughput"], "unit": UNIT, "n_gpus": 1, "steps": len(specs),
+            "warmup": 4, "ms_per_step": 1e3 * st["makespan_s"] / len(specs), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded request mix, Poisson arrivals)", "config": cfg,
-            "serve": {"p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "mean_s": summ["mean_s"],
-                      "makespan_s": summ["makespan_s"], "units": summ["units"],
-                      "hbm_budget_bytes": srv.adm.budget, "admitted_peak_bytes": srv.adm.peak,
-                      "batch_rebuilds": sum(g.rebuilds for g in srv.groups.values()),
-                      "quanta": srv.launch_quanta,
-                      "hbm_frac_whole_run": summ["throughput"] * bpu / 1e9 / peak},
-            "fp64_sequential": dict(seq64, rate_by_species=r64,
-                                    how="FIFO one request at a time; service = units / FP64 rate measured "
-                                        "on a 512x512 tube per species count"),
-            "fp32_unbatched_sequential": dict(seq32, rate_by_species=r32,
-                                              how="FIFO one request at a time; service = units / single-"
-                                                  "problem FP32 rate measured on a 512x512 tube"),
-            "clocks": clk, "e2e": {"value": summ["throughput"], "unit": UNIT, "h2d_bytes_per_step": 0,
+            "data": "synthetic (seeded request mix, Poisson arrivals)", "config": cfg, "serve": st,
+            "extrapolated_sequential": {
+                "fp64": dict(SV.simulate_sequential(timed, r64), rate_by_species=r64),
+                "fp32_unbatched": dict(SV.simulate_sequential(timed, r32), rate_by_species=r32),
+                "how": "not a run: FIFO queue over the whole mix with service time = updates / rate measured on "
+                       "a 512x512 tube per species count"},
+            "clocks": clk, "e2e": {"value": st["throughput"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                    "d2h_bytes_per_step": 8 * (max(nss) + 4)},
-            "roofline": {"bound": "hbm", "achieved": summ["throughput"] * bpu / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": summ["throughput"] * bpu / 1e9 / peak, "traffic": None,
+            "roofline": {"bound": "hbm", "achieved": st["throughput"] * bpu / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": st["throughput"] * bpu / 1e9 / peak, "traffic": None,
                          "kernel": "all step kernels of the run (whole-run average)",
                          "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+# Arithmetic variants of the precision studies: name -> (precision, options)
+STUDY_VARIANTS = {
+    "fp64": ("fp64", {}),
+    "fp32": ("fp32", {}),
+    "fp32_thermo64": ("fp32", {"thermo": "fp64"}),
+    "fp32_stochastic": ("fp32", {"rounding": "stochastic"}),
+    "fp32_thermo64_stochastic": ("fp32", {"thermo": "fp64", "rounding": "stochastic"}),
+    "bf16dev": ("bf16dev", {}),
+}
+
+
 def run_precision(args, D, dev):
-    """Precision study: the same initial state advanced in FP64, FP32 and
-    BF16DEV (the latter only where its scope allows), relative L2 and
-    L-infinity errors of the mixture fields against FP64 at checkpoints, and
-    each precision's drift of the conserved totals over the run."""
+    """Precision study: the same initial state advanced in FP64 and in the
+    float variants (FP32 with its thermo and rounding options, BF16DEV where
+    its scope allows); relative L2 and L-infinity errors of the mixture
+    fields against FP64 at checkpoints, each variant's drift of the conserved
+    totals at the same checkpoints, and the step time of each variant."""
     import torch
 
     from paper_2006_15932_gb300 import workloads as W
@@ -392,46 +450,58 @@ def run_precision(args, D, dev):
         nx, ny = (int(v) for v in (args.grid or "4096x4096").lower().split("x"))
         pb = W.kh_shear_layer(nx, ny=ny)
         total = args.study_steps or 1000
-        precs = ["fp64", "fp32", "bf16dev"]
+        precs = ["fp64", "fp32", "fp32_thermo64", "fp32_stochastic", "bf16dev"]
         checkpoints = 4
     else:
         nx, ny = (int(v) for v in (args.grid or "1024x256").lower().split("x"))
         pb = W.reactive_premixed(nx, ny)
         total = args.study_steps or 20000
-        precs = ["fp64", "fp32"]
+        precs = ["fp64", "fp32", "fp32_thermo64", "fp32_stochastic", "fp32_thermo64_stochastic"]
         checkpoints = 10
     st = torch.cuda.Stream(device=dev)
     sols = {}
     with torch.cuda.stream(st):
         for p in precs:
-            sols[p] = D.Solver(pb, p, device=dev)
+            prec, opts = STUDY_VARIANTS[p]
+            sols[p] = D.Solver(pb, prec, device=dev, **opts)
             sols[p].set_state()
         cons0 = {p: sols[p].conservation().cpu().numpy() for p in precs}
     S = pb.ns
     names = ["rho", "ux", "uy", "T"]
     rows = {"rho": 4 * S, "ux": 4 * S + 1, "uy": 4 * S + 2, "T": 4 * S + 3}
+
+    def drift_of(c1, c0):
+        mass0 = float(sum(abs(c0[:S])))
+        e_scale = abs(float(c0[S + 2])) + abs(float(c0[S + 3]))
+        return {"mass": float((sum(c1[:S]) - sum(c0[:S])) / mass0),
+                "momentum_x": float((c1[S] - c0[S]) / mass0),
+                "momentum_y": float((c1[S + 1] - c0[S + 1]) / mass0),
+                "energy_plus_bound_heat": float(((c1[S + 2] + c1[S + 3]) - (c0[S + 2] + c0[S + 3])) / e_scale)}
+
     # velocity errors are measured against the velocity scale of the run
     # (max |u| of the FP64 field, at least the sound speed 1), not against a
     # field that may vanish
     curve = []
     per = total // checkpoints
     done = 0
-    t_fp64 = 0.0
+    t_step = {p: 0.0 for p in precs}
     while done < total:
         n = min(per, total - done)
+        mom = {}
         with torch.cuda.stream(st):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            sols["fp64"].step(n)
-            e1.record(st)
-            for p in precs[1:]:
+            for p in precs:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
                 sols[p].step(n)
-            mom = {p: sols[p].moments() for p in precs}
+                e1.record(st)
+                e1.synchronize()
+                t_step[p] += e0.elapsed_time(e1) * 1e-3
+                mom[p] = sols[p].moments()
+            cons = {p: sols[p].conservation().cpu().numpy() for p in precs}
         st.synchronize()
-        t_fp64 += e0.elapsed_time(e1) * 1e-3
         done += n
         ref = mom["fp64"]
-        entry = {"step": done}
+        entry = {"step": done, "drift": {p: drift_of(cons[p], cons0[p]) for p in precs}}
         for p in precs[1:]:
             errs = {}
             for nm in names:
@@ -448,29 +518,23 @@ def run_precision(args, D, dev):
             entry[p] = errs
         curve.append(entry)
         del mom, ref
-    drift = {}
-    with torch.cuda.stream(st):
-        for p in precs:
-            c1 = sols[p].conservation().cpu().numpy()
-            c0 = cons0[p]
-            mass0 = float(sum(abs(c0[:S])))
-            e_scale = abs(float(c0[S + 2])) + abs(float(c0[S + 3]))
-            drift[p] = {"mass": float(abs(sum(c1[:S]) - sum(c0[:S])) / mass0),
-                        "momentum_x": float(abs(c1[S] - c0[S]) / mass0),
-                        "momentum_y": float(abs(c1[S + 1] - c0[S + 1]) / mass0),
-                        "energy_plus_bound_heat": float(abs((c1[S + 2] + c1[S + 3]) - (c0[S + 2] + c0[S + 3]))
-                                                        / e_scale)}
     for p in precs:
         rc, bits = sols[p].status()
         if rc != 0:
             raise SystemExit(f"health flag raised in {p}: bits={bits}")
         sols[p].close()
+    final = curve[-1]["drift"]
     line = {"study": args.workload, "grid": [pb.nx, pb.ny], "species": S, "steps": total,
             "boundary": ["periodic" if b == 0 else "outflow" for b in (pb.bc_x, pb.bc_y)],
-            "reactive": pb.k_ov != 0.0, "fp64_seconds": t_fp64,
-            "error_vs_fp64": curve, "conservation_drift": drift,
+            "reactive": pb.k_ov != 0.0,
+            "variants": {p: {"precision": STUDY_VARIANTS[p][0], **STUDY_VARIANTS[p][1]} for p in precs},
+            "updates_per_s": {p: pb.nx * pb.ny * S * total / t_step[p] for p in precs},
+            "error_vs_fp64": curve, "conservation_drift": final,
+            "conservation_drift_minus_fp64": {p: {k: final[p][k] - final["fp64"][k] for k in final[p]}
+                                              for p in precs},
             "norms": "rel_linf = max|a-b| / max|b|, rel_l2 = ||a-b|| / ||b||; for u_x, u_y the scale is "
-                     "max(max|u|, 1) (and rms of that scale for L2)"}
+                     "max(max|u|, 1) (and rms of that scale for L2); drift = (total(t) - total(0)) / scale, "
+                     "signed; the energy total includes the heat bound in the fuel"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -618,6 +682,16 @@ def main():
         e2e = measure_e2e(D, pb, args.precision, dev, stream)
         if args.precision == "fp32" and rank == 0:
             extras["fp64"] = measure_fp64(D, pb, dev, stream)
+    if not args.no_extras and args.workload == "kh4096" and args.precision == "fp32" and rank == 0:
+        from paper_2006_15932_gb300 import workloads as W
+
+        # a short serving run of a smaller request mix (sides 128..512, 500..2000
+        # steps), so that latency percentiles and the sequential-FP64 baseline
+        # appear beside the step throughput
+        mix = W.serving_requests(48, seed=W.SEED + 2, lo=128, hi=512, steps=(500, 2000))
+        extras["serve"] = dict(serve_study(D, dev, mix, 0.8, 128, subset_n=8),
+                               mix="48 requests: sides log-uniform 128..512, 2-4 species, half reactive, "
+                                   "500..2000 steps, seeded")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -642,34 +716,32 @@ def main():
 
 
 def measure_e2e(D, pb, precision, dev, stream, n_inner=50, reps=6, lanes=2):
-    """End to end through the public API: pinned host fields -> device,
-    dbm_set_state, n_inner dbm_step, dbm_moments, moments -> pinned host.
-    Every solve copies its inputs in and its result out.  Solves run on
-    `lanes` streams, each with its own solver and buffers, issued in turn,
-    so that one solve's copies overlap another's kernels, as a caller
-    serving a stream of solves would run them; the value counts the updates
-    of all `reps` solves over the wall time from the first issue to the last
-    result on the host."""
+    """End to end through the C ABI with host buffers, as a caller without
+    device-side field buffers would use it: every solve hands the library
+    page-locked host pointers, so dbm_set_state reads the initial fields
+    (rho^s, u_x, u_y, T) straight from host memory, n_inner dbm_step follow,
+    and dbm_moments writes the (4S+5) FP64 output fields straight into
+    page-locked host memory.  Solves run on `lanes` streams, each with its
+    own solver and output buffer, issued in turn, so that one solve's
+    host transfers overlap another's steps; the value counts the updates of
+    all `reps` solves over the wall time from the first issue to the last
+    result on the host.  Bytes per step are each solve's host-to-device and
+    device-to-host bytes divided by its n_inner steps."""
     import torch
 
-    host = [torch.from_numpy(a.astype("float64")).pin_memory() for a in (pb.rho_s, pb.ux, pb.uy, pb.T)]
+    host = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+            for a in (pb.rho_s, pb.ux, pb.uy, pb.T)]
     streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(lanes - 1)]
     lane = []
     for st in streams:
-        with torch.cuda.stream(st):
-            lane.append({"stream": st, "solver": D.Solver(pb, precision, device=dev),
-                         "dev_in": [torch.empty(h.shape, dtype=torch.float64, device=dev) for h in host],
-                         "dev_out": torch.empty((4 * pb.ns + 5, pb.ny, pb.nx), dtype=torch.float64, device=dev),
-                         "out_host": torch.empty((4 * pb.ns + 5, pb.ny, pb.nx), dtype=torch.float64).pin_memory()})
+        lane.append({"stream": st, "solver": D.Solver(pb, precision, device=dev, stream=st),
+                     "out_host": torch.empty((4 * pb.ns + 5, pb.ny, pb.nx), dtype=torch.float64).pin_memory()})
 
     def issue(L):
-        with torch.cuda.stream(L["stream"]):
-            for d, h in zip(L["dev_in"], host):
-                d.copy_(h, non_blocking=True)
-            L["solver"].set_state(*L["dev_in"])
-            L["solver"].step(n_inner)
-            L["solver"].moments(L["dev_out"])
-            L["out_host"].copy_(L["dev_out"], non_blocking=True)
+        h, st = L["solver"].h, L["stream"].cuda_stream
+        D.dbm_set_state(h, *[t.data_ptr() for t in host], st)
+        D.dbm_step(h, n_inner, st)
+        D.dbm_moments(h, L["out_host"].data_ptr(), st)
 
     for L in lane:  # warm-up
         issue(L)
@@ -683,10 +755,11 @@ def measure_e2e(D, pb, precision, dev, stream, n_inner=50, reps=6, lanes=2):
         L["solver"].close()
     h2d = sum(h.numel() * 8 for h in host)
     d2h = lane[0]["out_host"].numel() * 8
-    return {"value": pb.nx * pb.ny * pb.ns * n_inner / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h,
-            "step": f"one solve: host fields in, dbm_set_state, {n_inner} dbm_step, dbm_moments, host out; "
-                    f"{reps} solves on {lanes} streams, host wall time"}
+    return {"value": pb.nx * pb.ny * pb.ns * n_inner / dt, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / n_inner, "d2h_bytes_per_step": d2h / n_inner,
+            "h2d_bytes_per_solve": h2d, "d2h_bytes_per_solve": d2h, "steps_per_solve": n_inner,
+            "step": f"one solve: dbm_set_state from page-locked host fields, {n_inner} dbm_step, "
+                    f"dbm_moments into page-locked host memory; {reps} solves on {lanes} streams, host wall time"}
 
 
 def measure_fp64(D, pb, dev, stream, steps=10):

@@ -44,14 +44,47 @@ extern "C" {
 
 enum dbm_bc { DBM_BC_PERIODIC = 0, DBM_BC_OUTFLOW = 1 };
 
-/* Arithmetic and storage of the stepped state.
+/* Arithmetic and storage of the stepped state.  Every output array is
+ * FP64.  dbm_nonequilibrium and dbm_conservation are computed in double in
+ * every mode; dbm_moments in double for DBM_FP64 and, for the float states,
+ * in float (their own precision) with the temperature subtraction in
+ * float-float.
  *  DBM_FP64    f stored and stepped in double.
- *  DBM_FP32    f stored and stepped in float; the mixture temperature (from
- *              the energy moment), the Arrhenius rate and all reported
- *              outputs are computed in double.
+ *  DBM_FP32    f stored and stepped in float.  By default (DBM_THERMO_FLOATFLOAT)
+ *              the species and mixture moment sums are float; the one
+ *              cancelling subtraction of the mixture temperature, energy
+ *              minus kinetic part, is carried in float-float (an error-free
+ *              FMA product and Knuth's two-sum, on the FP32 pipes), and the
+ *              Arrhenius rate uses float expf.  DBM_THERMO_FP64 computes the
+ *              species moments, the mixture u and T (the temperature
+ *              recovery from the energy moment, section "Discrete Boltzmann
+ *              model") and the Arrhenius rate in double from the stored
+ *              floats instead; the equilibrium, collision and advection stay
+ *              float.  dbm_params.rounding selects round-to-nearest or
+ *              stochastic rounding of the stored f.
  *  DBM_BF16DEV f stored as a bfloat16 deviation from the equilibrium of
  *              stored float moments (n^s, u, T), stepped in float. */
 enum dbm_precision { DBM_FP64 = 0, DBM_FP32 = 1, DBM_BF16DEV = 2 };
+
+/* Arithmetic options of the DBM_FP32 step (dbm_params.thermo and
+ * dbm_params.rounding); both need S <= 4, a TMA-staged step kernel, and
+ * cannot be batched.  The defaults run the fastest kernel. */
+enum dbm_thermo {
+    DBM_THERMO_FLOATFLOAT = 0, /* float moment sums, float-float temperature subtraction */
+    DBM_THERMO_FP64 = 1        /* species moments, mixture u, T and the Arrhenius
+                                  rate in double                                   */
+};
+enum dbm_rounding {
+    DBM_ROUND_NEAREST = 0,     /* f^{n+1} = f^n + increment, rounded to nearest */
+    DBM_ROUND_STOCHASTIC = 1   /* the exact sum f^n + increment (two-sum) and the
+                                  reacted density n* rounded up or down at random
+                                  with the probabilities that make the rounding
+                                  unbiased, so rounding errors do not accumulate
+                                  into a drift of the conserved totals; random
+                                  numbers from a counter-based hash of (step,
+                                  cell, value): deterministic for a given step
+                                  count                                         */
+};
 
 enum dbm_status_code {
     DBM_OK = 0,
@@ -112,6 +145,14 @@ typedef struct dbm_params {
     double accel[2];        /* external acceleration a of the force term; 0 = off   */
     int precision;          /* dbm_precision                                         */
     int step_kernel;        /* dbm_step_kernel; all give bitwise identical results   */
+    int wait_polls;         /* polls of a TMA-staged step's first wait for its tile
+                               copy: 0 = library default (2^22), > 0 = that many,
+                               < 0 = none (the wait gives up at once, the step
+                               raises DBM_HEALTH_TIMEOUT and writes nothing: a
+                               safe way to exercise the timeout path; the copy
+                               still lands before the CTA exits)               */
+    int thermo;             /* dbm_thermo (DBM_FP32 only)                          */
+    int rounding;           /* dbm_rounding (DBM_FP32 only)                        */
     dbm_species sp[DBM_MAX_SPECIES];
 } dbm_params;
 
@@ -196,7 +237,11 @@ int dbm_step(dbm_handle *h, int nsteps, void *stream);
  *   rows 4s..4s+3: n^s, u^s_x, u^s_y, T^s = m^s (E^s/n^s - u^s.u^s)/(D+I^s)
  *   (u^s = T^s = 0 for an absent species, n^s = 0);
  *   rows 4S..4S+4: rho = sum m^s n^s, u_x, u_y, T (mixture, from conservation
- *   of the collision term), p = n T with n = sum n^s.  Async on stream. */
+ *   of the collision term), p = n T with n = sum n^s.
+ * Evaluated in double for a DBM_FP64 state; for DBM_FP32 and DBM_BF16DEV
+ * states in float (ring sums as in the step, the mixture temperature's
+ * subtraction in float-float), a few float ulps from the exact moments of
+ * the stored floats.  Async on stream. */
 int dbm_moments(dbm_handle *h, double *out, void *stream);
 
 /* Nonequilibrium moments, FP64 out[20 S][ny][nx], 20 rows per species s
@@ -238,7 +283,8 @@ int dbm_batch_table_bytes(dbm_handle *const *handles, int n, size_t *bytes);
 
 /* Build a batch over n handles; writes the table (async on stream, then
  * synchronises it).  DBM_ERR_INVALID if a handle is unbound, not FP32, has
- * S > 4 or a different S than the others, or the table is too small. */
+ * S > 4 or a different S than the others, asks for a non-default thermo or
+ * rounding option, or the table is too small. */
 int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t table_bytes, void *stream,
                      dbm_batch **out);
 

@@ -8,6 +8,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dbm_internal.h"
 
 namespace dbm {
@@ -270,6 +272,14 @@ static int validate(dbm_handle *h, const dbm_params &p)
         return fail(h, DBM_ERR_INVALID,
                     "BF16DEV storage is built for up to 4 species without reaction or force "
                     "(its reference equilibrium is that of the stored moments)");
+    if (p.thermo != DBM_THERMO_FLOATFLOAT && p.thermo != DBM_THERMO_FP64)
+        return fail(h, DBM_ERR_INVALID, "unknown thermo option %d", p.thermo);
+    if (p.rounding != DBM_ROUND_NEAREST && p.rounding != DBM_ROUND_STOCHASTIC)
+        return fail(h, DBM_ERR_INVALID, "unknown rounding option %d", p.rounding);
+    if ((p.thermo != DBM_THERMO_FLOATFLOAT || p.rounding != DBM_ROUND_NEAREST) &&
+        (p.precision != DBM_FP32 || p.nspecies > 4 || p.step_kernel == DBM_KERNEL_GENERIC))
+        return fail(h, DBM_ERR_INVALID,
+                    "the thermo and rounding options are built for the TMA-staged FP32 step (up to 4 species)");
     if (!isfinite(p.accel[0]) || !isfinite(p.accel[1]))
         return fail(h, DBM_ERR_INVALID, "acceleration must be finite");
     double vmax = 0.0;
@@ -463,8 +473,9 @@ int dbm_bind(dbm_handle *h, void *f_a, void *f_b, void *scratch)
     h->bound = 1;
     make_tensor_maps(h);
     const int want = h->p.step_kernel;
-    if (want != DBM_KERNEL_AUTO && want != DBM_KERNEL_GENERIC && !h->tma_ok)
-        return fail(h, DBM_ERR_INVALID, "the TMA-staged step kernel is built for FP32 with at most 4 species");
+    if ((want != DBM_KERNEL_AUTO && want != DBM_KERNEL_GENERIC) || uses_acc(h->p))
+        if (!h->tma_ok)
+            return fail(h, DBM_ERR_INVALID, "the TMA-staged step kernel is built for FP32 with at most 4 species");
     return DBM_OK;
 }
 
@@ -516,13 +527,15 @@ int dbm_step(dbm_handle *h, int nsteps, void *stream)
     if (rc) return rc;
     if (nsteps < 0) return fail(h, DBM_ERR_INVALID, "nsteps=%d < 0", nsteps);
     cudaStream_t st = (cudaStream_t)stream;
-    for (int t = 0; t < nsteps; ++t) {
+    nvtxRangePushA("dbm_step");  // host-side range over the enqueueing of the launches
+    for (int t = 0; t < nsteps && rc == DBM_OK; ++t) {
         rc = launch_step(h, h->cur, st);
-        if (rc) return rc;
+        if (rc) break;
         h->cur ^= 1;
         h->steps += 1;
     }
-    return DBM_OK;
+    nvtxRangePop();
+    return rc;
 }
 
 int dbm_moments(dbm_handle *h, double *out, void *stream)

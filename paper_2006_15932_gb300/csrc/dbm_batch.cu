@@ -23,16 +23,60 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dbm_step_impl.cuh"
 
 namespace dbm {
 
+// The constants of one instance that step_cell reads from the instance's
+// own block (`g`: geometry, boundaries, reaction, force, wait limit); the
+// rest of StepConsts is shared by every instance of a launch.
+template <int S>
+struct InstConsts {
+    float tau_d[S], tau_a[S];  // tau^s, tau^s a^s
+    float k_ov, Ea_over_R, Qheat, src;
+    float accel_x, accel_y;
+    int fuel, oxid, has_reaction, has_force;
+    int nx, ny, pitch, bc_x, bc_y, wait_polls;
+    long long plane;
+};
+
+template <int S>
+InstConsts<S> inst_part(const StepConsts<float, S> &c)
+{
+    InstConsts<S> g;
+    memset(&g, 0, sizeof(g));
+    for (int s = 0; s < S; ++s) {
+        g.tau_d[s] = c.tau_d[s];
+        g.tau_a[s] = c.tau_a[s];
+    }
+    g.k_ov = c.k_ov;
+    g.Ea_over_R = c.Ea_over_R;
+    g.Qheat = c.Qheat;
+    g.src = c.src;
+    g.accel_x = c.accel_x;
+    g.accel_y = c.accel_y;
+    g.fuel = c.fuel;
+    g.oxid = c.oxid;
+    g.has_reaction = c.has_reaction;
+    g.has_force = c.has_force;
+    g.nx = c.nx;
+    g.ny = c.ny;
+    g.pitch = c.pitch;
+    g.bc_x = c.bc_x;
+    g.bc_y = c.bc_y;
+    g.wait_polls = c.wait_polls;
+    g.plane = c.plane;
+    return g;
+}
+
 // One instance of a launch: its input descriptor at the launch's parity,
-// step constants and outputs.
+// own constants and outputs.
 template <int S>
 struct __align__(128) BatchInst {  // CUtensorMap is 128-byte aligned
     CUtensorMap tmap;
-    StepConsts<float, S> c;
+    InstConsts<S> c;
     const float *fin;  // the input buffer (interior cells for a boundary tile's halo)
     float *fout;
     unsigned *flag;
@@ -67,6 +111,7 @@ void hot_part(StepConsts<float, S> &c)
     c.fuel = c.oxid = c.has_reaction = c.has_force = 0;
     c.accel_x = c.accel_y = 0.f;
     c.nx = c.ny = c.pitch = c.bc_x = c.bc_y = 0;
+    c.wait_polls = 0;
     c.plane = 0;
 }
 
@@ -107,8 +152,14 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
         if (t + 1 < t1) next = tiles[t + 1];
         const BatchInst<S> &e = P.e[cur.k];
         __syncthreads();  // barrier initialised / previous tile no longer read
-        if (leader) tma_tile_load(tile, reinterpret_cast<unsigned long long>(&e.tmap), cur.bx0, cur.by0, b, BYTES);
-        const bool ok = mbar_wait(b, phase, TMA_WAIT_LIMIT);
+        if (leader) {
+            // the previous tile's halo fill and stencil reads went through the
+            // generic proxy; order them before the async-proxy copy that
+            // overwrites the same shared memory
+            if (t > t0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_tile_load(tile, reinterpret_cast<unsigned long long>(&e.tmap), cur.bx0, cur.by0, b, BYTES);
+        }
+        const bool ok = mbar_wait(b, phase, e.c.wait_polls);
         if (__syncthreads_or(!ok)) {
             // the copy did not land: report, give it one more bounded wait so
             // that no copy is left writing into shared memory, leave together
@@ -116,7 +167,7 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
             mbar_wait(b, phase, TMA_WAIT_LIMIT);
             return;
         }
-        const StepConsts<float, S> &g = e.c;
+        const InstConsts<S> &g = e.c;
         fill_tile_halo<NP, TX, TY>(tile, e.fin, cur.bx0, cur.by0, g.nx, g.ny, g.pitch, g.plane, g.bc_x, g.bc_y,
                                    ty * (TX / CW) + tx, NT);
         const int x = cur.bx0 + CW * tx, y = cur.by0 + ty;
@@ -307,7 +358,7 @@ static int write_tables(dbm_batch *b, cudaStream_t st)
                            b->promote ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                     return bfail(b, DBM_ERR_CUDA, "tensor map encoding failed");
-                e.c = cs[k];
+                e.c = inst_part<S>(cs[k]);
                 e.fin = (const float *)in;
                 e.fout = (float *)h->f[h->cur ^ par ^ 1];
                 e.flag = (unsigned *)h->scratch;
@@ -449,7 +500,8 @@ int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t tabl
     const int S = handles[0] ? handles[0]->p.nspecies : 0;
     for (int k = 0; k < n; ++k) {
         const dbm_handle *h = handles[k];
-        if (!h || !h->bound || h->p.precision != DBM_FP32 || h->p.nspecies != S || S > 4 || !h->tma_ok)
+        if (!h || !h->bound || h->p.precision != DBM_FP32 || h->p.nspecies != S || S > 4 || !h->tma_ok ||
+            uses_acc(h->p))
             return DBM_ERR_INVALID;
     }
     if (table_bytes < table_size(handles, n) || ((uintptr_t)table & 127)) return DBM_ERR_INVALID;
@@ -528,10 +580,19 @@ int dbm_batch_tune(dbm_batch *b, void *stream, int reps)
     return rebuild(b, st);
 }
 
+static int batch_step(dbm_batch *b, int nsteps, cudaStream_t st);
+
 int dbm_batch_step(dbm_batch *b, int nsteps, void *stream)
 {
     if (!b || nsteps < 0) return DBM_ERR_INVALID;
-    cudaStream_t st = (cudaStream_t)stream;
+    nvtxRangePushA("dbm_batch_step");  // host-side range over the enqueueing of the steps
+    const int rc = batch_step(b, nsteps, (cudaStream_t)stream);
+    nvtxRangePop();
+    return rc;
+}
+
+static int batch_step(dbm_batch *b, int nsteps, cudaStream_t st)
+{
     for (size_t k = 0; k < b->h.size(); ++k)
         if (b->h[k]->steps != b->expected_steps[k]) {  // a handle was reset or stepped alone
             const int rc = rebuild(b, st);

@@ -112,6 +112,10 @@ struct BfSrc {
 #pragma unroll
         for (int i = 0; i < Q; ++i) v[i] = (double)f[i];
     }
+    __device__ __forceinline__ void load16f(int s, long long cell, float v[Q]) const
+    {
+        bf_cell_f<S>(k, st, s, cell, v);
+    }
 };
 
 inline BfState bf_state(const dbm_handle *h, void *buf)

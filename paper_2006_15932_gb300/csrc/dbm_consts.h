@@ -73,7 +73,49 @@ void fill_step_consts(const dbm_handle *h, StepConsts<real, S> &c)
     c.pitch = h->lay.pitch;
     c.bc_x = p.bc_x;
     c.bc_y = p.bc_y;
+    c.wait_polls = p.wait_polls == 0 ? TMA_WAIT_POLLS : p.wait_polls < 0 ? 0 : p.wait_polls;
     c.plane = h->lay.plane;
+}
+
+// Integer hash "lowbias32" (C. Wellons' hash-prospector: xor-shift /
+// multiply rounds with its published constants); seeds and random numbers
+// of the stochastic rounding.
+__host__ __device__ inline unsigned mix32(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+template <int S>
+void fill_acc_consts(const dbm_handle *h, const StepConsts<float, S> &c, AccConsts<S> &a)
+{
+    memset(&a, 0, sizeof(a));
+    const dbm_params &p = h->p;
+    a.thermo64 = p.thermo == DBM_THERMO_FP64;
+    a.stochastic = p.rounding == DBM_ROUND_STOCHASTIC;
+    a.seed = mix32((unsigned)h->steps * 0x9e3779b9u + 0x632be5abu) ^ mix32((unsigned)(h->steps >> 32));
+    double src = 0.0;
+    for (int s = 0; s < S; ++s) {
+        for (int r = 0; r < 4; ++r) {
+            a.vr[s][r] = (double)c.vr[s][r];
+            a.qr[s][r] = (double)c.qr[s][r];
+        }
+        // the weights of the float step as exact doubles (lam_h + lam_l)
+        a.lam[s] = (double)c.lam_h[s] + (double)c.lam_l[s];
+        a.kap[s] = (double)c.kap_h[s] + (double)c.kap_l[s];
+        a.dpi[s] = (double)c.dpi[s];
+        a.tau_a[s] = p.sp[s].tau * p.sp[s].a_stoich;
+        a.tau_d[s] = p.sp[s].tau;
+        src += (2.0 + p.sp[s].I) * p.sp[s].a_stoich;
+    }
+    a.k_ov = p.k_ov;
+    a.Ea_over_R = p.Ea_over_R;
+    a.Qheat = p.Q;
+    a.src = src;
 }
 
 template <int S>

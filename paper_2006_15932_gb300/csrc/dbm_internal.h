@@ -16,6 +16,10 @@ constexpr int GX = 4;  // ghost columns left of the interior (2 used; 4 keep row
 constexpr int GY = 2;  // ghost rows above and below the interior
 constexpr int CONS_BLOCKS = 512;          // fixed grid of the conservation reduction
 constexpr size_t SCRATCH_HEAD = 256;      // health flag area at the start of scratch
+// polls of an mbarrier wait for a tile copy before it gives up (each poll
+// may suspend the thread for a while); the first wait of a step can be
+// shortened per handle (dbm_params.wait_polls), the drain wait cannot
+constexpr int TMA_WAIT_POLLS = 1 << 22;
 
 // Direction of velocity i inside its ring: rings a, c (i/4 even) lie on the
 // axes, rings b, d (i/4 odd) on the diagonals (D2V16 definition).
@@ -55,7 +59,29 @@ struct StepConsts {
     int fuel, oxid;
     int has_reaction, has_force;
     int nx, ny, pitch, bc_x, bc_y;
+    int wait_polls;  // polls of the first wait for the tile copy (TMA-staged steps)
     long long plane;
+};
+
+// Extra kernel parameters of the FP32 step with its arithmetic options
+// (dbm_params.thermo, dbm_params.rounding): the run-time switches, the
+// seed of the stochastic rounding for this launch, and the constants of the
+// FP64 moment and rate evaluation (the float constants of StepConsts
+// widened, so that both evaluations use the same discrete velocities and
+// weights).  NoAcc stands in for it in the default kernels.
+template <int S>
+struct AccConsts {
+    static constexpr bool on = true;
+    int thermo64;    // DBM_THERMO_FP64
+    int stochastic;  // DBM_ROUND_STOCHASTIC
+    unsigned seed;   // per launch: hash of the handle's step count
+    double vr[S][4], qr[S][4];  // ring speeds and v.v + eta^2, as the float step uses them
+    double lam[S], kap[S];      // mixture weights m dt_tau and lam dpi / m
+    double dpi[S], tau_a[S], tau_d[S];
+    double k_ov, Ea_over_R, Qheat, src;
+};
+struct NoAcc {
+    static constexpr bool on = false;
 };
 
 // Kernel parameters of the FP64 output / initialisation kernels.
@@ -150,6 +176,13 @@ int launch_conservation_noalloc(dbm_handle *h, const void *f, double *out, cudaS
 
 template <typename real, int S>
 void fill_step_consts(const dbm_handle *h, StepConsts<real, S> &c);
+template <int S>
+void fill_acc_consts(const dbm_handle *h, const StepConsts<float, S> &c, AccConsts<S> &a);
+// the FP32 step runs the kernel with the arithmetic options
+inline bool uses_acc(const dbm_params &p)
+{
+    return p.precision == DBM_FP32 && (p.thermo != DBM_THERMO_FLOATFLOAT || p.rounding != DBM_ROUND_NEAREST);
+}
 template <int S>
 void fill_out_consts(const dbm_handle *h, OutConsts<S> &c);
 

@@ -10,8 +10,24 @@ namespace dbm {
 
 template <int S>
 int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st);
-template <int S, int TX, int TY, int CW>
+template <int S, int TX, int TY, int CW, bool ACC>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st);
+
+// The TMA-staged step of the handle's tile, with (ACC) or without the FP32
+// arithmetic options.
+template <bool ACC>
+static int launch_tma(dbm_handle *h, const CUtensorMap *tm, const void *fin, void *fout, cudaStream_t st)
+{
+    switch (h->p.nspecies) {
+    case 1: return launch_step_tma_t<1, tma_tile_x(1), tma_tile_y(1), 1, ACC>(h, tm, fin, fout, st);
+    case 2:
+        if (h->tma_cw == 2) return launch_step_tma_t<2, PAIR_TX, PAIR_TY, 2, ACC>(h, tm, fin, fout, st);
+        return launch_step_tma_t<2, tma_tile_x(2), tma_tile_y(2), 1, ACC>(h, tm, fin, fout, st);
+    case 3: return launch_step_tma_t<3, tma_tile_x(3), tma_tile_y(3), 1, ACC>(h, tm, fin, fout, st);
+    case 4: return launch_step_tma_t<4, tma_tile_x(4), tma_tile_y(4), 1, ACC>(h, tm, fin, fout, st);
+    }
+    return DBM_ERR_INVALID;
+}
 
 bool tma_supported(const dbm_params &p) { return p.precision == DBM_FP32 && p.nspecies <= 4; }
 
@@ -92,15 +108,9 @@ int launch_step(dbm_handle *h, int cur, cudaStream_t st)
     const int want = h->p.step_kernel;
     if (h->tma_ok && want != DBM_KERNEL_GENERIC) {
         const CUtensorMap *tm = &h->tmap[cur];
-        switch (h->p.nspecies) {
-        case 1: return launch_step_tma_t<1, tma_tile_x(1), tma_tile_y(1), 1>(h, tm, fin, fout, st);
-        case 2:
-            if (h->tma_cw == 2) return launch_step_tma_t<2, PAIR_TX, PAIR_TY, 2>(h, tm, fin, fout, st);
-            return launch_step_tma_t<2, tma_tile_x(2), tma_tile_y(2), 1>(h, tm, fin, fout, st);
-        case 3: return launch_step_tma_t<3, tma_tile_x(3), tma_tile_y(3), 1>(h, tm, fin, fout, st);
-        case 4: return launch_step_tma_t<4, tma_tile_x(4), tma_tile_y(4), 1>(h, tm, fin, fout, st);
-        }
+        return uses_acc(h->p) ? launch_tma<true>(h, tm, fin, fout, st) : launch_tma<false>(h, tm, fin, fout, st);
     }
+    if (uses_acc(h->p)) return DBM_ERR_INVALID;  // the options exist in the TMA-staged kernel only
     if (want != DBM_KERNEL_AUTO && want != DBM_KERNEL_GENERIC) return DBM_ERR_INVALID;
     if (h->p.precision == DBM_BF16DEV) return launch_step_bf16(h, cur, st);
     if (h->p.precision == DBM_FP64) return launch_step_f64(h, cur, st);

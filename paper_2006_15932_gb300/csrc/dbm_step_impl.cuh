@@ -46,6 +46,8 @@
 #pragma once
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "dbm_consts.h"
 #include "dbm_device.cuh"
 
@@ -228,10 +230,19 @@ __device__ __forceinline__ V resid4(const float k[4], V c0, V c1, V c2, V c3, V 
     return vfma(bc<V>(-k[3]), c3, vfma(bc<V>(-k[2]), c2, vfma(bc<V>(-k[1]), c1, vfma(bc<V>(-k[0]), c0, t))));
 }
 
+__device__ __forceinline__ float sr_round(double x, float u);
+__device__ __forceinline__ float sr_uniform(unsigned h, int k);
+
 // Solve the symmetry blocks (out: ring means A[4], B[2], H[2], X[4], Y[4])
-// and project the result onto exact mass, energy and momentum.
-template <class V, class K>
-__device__ __forceinline__ void solve_blocks(const K &k, int s, const V c[16], V o[16])
+// and project the result onto exact mass, energy and momentum.  With SR the
+// projected ring means, which carry the equilibrium's mass and energy, are
+// formed exactly (in double) and rounded stochastically (random numbers
+// kb..kb+3 of the cell hashes h): a round-to-nearest result misses the mass
+// target by a rounding error that follows the slowly varying macroscopic
+// state, and so adds up over the steps instead of averaging out.
+template <class V, class K, bool SR = false>
+__device__ __forceinline__ void solve_blocks(const K &k, int s, const V c[16], V o[16], const unsigned *h = nullptr,
+                                             int kb = 0)
 {
 #pragma unroll
     for (int r = 0; r < 4; ++r) o[r] = dot4<V>(k.eqA[s][r], c[0], c[1], c[2], c[3]);
@@ -253,7 +264,17 @@ __device__ __forceinline__ void solve_blocks(const K &k, int s, const V c[16], V
     const V dy = resid4<V>(k.wv[s], o[12], o[13], o[14], o[15], c[12]);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        o[r] = vfma(bc<V>(k.eqA[s][r][1]), de, vfma(bc<V>(k.eqA[s][r][0]), dm, o[r]));
+        if constexpr (SR) {
+            using L = Lanes<V>;
+#pragma unroll
+            for (int j = 0; j < L::n; ++j) {
+                const double x = fma((double)k.eqA[s][r][1], (double)L::get(de, j),
+                                     fma((double)k.eqA[s][r][0], (double)L::get(dm, j), (double)L::get(o[r], j)));
+                L::set(o[r], j, sr_round(x, sr_uniform(h[j], kb + r)));
+            }
+        } else {
+            o[r] = vfma(bc<V>(k.eqA[s][r][1]), de, vfma(bc<V>(k.eqA[s][r][0]), dm, o[r]));
+        }
         o[8 + r] = vfma(bc<V>(k.eqX[s][r][0]), dx, o[8 + r]);
         o[12 + r] = vfma(bc<V>(k.eqX[s][r][0]), dy, o[12 + r]);
     }
@@ -344,6 +365,87 @@ __device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux,
     return __fadd_rn(s, __fsub_rn(se, pe)) / wd;
 }
 
+// Stochastic rounding (dbm_params.rounding = DBM_ROUND_STOCHASTIC).  The
+// exact value is s + e with s its round-to-nearest float; the result is the
+// float neighbour of s on e's side with probability |e| / (spacing of the
+// floats there), else s, so that its expectation is exactly s + e.  u is
+// uniform in [0, 1).  Zero, infinite and NaN s are returned as they are.
+__device__ __forceinline__ float sr_finish(float s, float e, float u)
+{
+    if (e == 0.0f || s == 0.0f) return s;
+    const int away = (e > 0.0f) == (s > 0.0f) ? 1 : -1;  // one step away from zero, or towards it
+    const float nb = __int_as_float(__float_as_int(s) + away);
+    const float gap = fabsf(__fsub_rn(nb, s));
+    return fabsf(e) > __fmul_rn(u, gap) ? nb : s;
+}
+// a + b rounded stochastically: s + e = a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ float sr_add(float a, float b, float u)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return sr_finish(s, e, u);
+}
+// a double rounded stochastically to float (x - s is exact in double).
+__device__ __forceinline__ float sr_round(double x, float u)
+{
+    const float s = __double2float_rn(x);
+    return sr_finish(s, __double2float_rn(x - (double)s), u);
+}
+// The k-th uniform number in [0, 1) of a cell whose hash is h: a Weyl
+// sequence (golden-ratio increments) from h, top 24 bits.
+__device__ __forceinline__ float sr_uniform(unsigned h, int k)
+{
+    return __uint2float_rz((h + (unsigned)k * 0x9e3779b9u) >> 8) * 0x1p-24f;
+}
+
+// Mixture u, T of one cell (reading R1 of the collision's conservation)
+// and the species densities, evaluated in double from the stored floats
+// of the tile (dbm_params.thermo = DBM_THERMO_FP64): ring sums, species
+// moments, weighted sums, u = sum lam j / sum lam n and
+// T = (sum lam E - u.u sum lam n) / sum kap n.  Lane j of the tile's values.
+template <int S, class Tile, class X>
+__device__ __forceinline__ void moments_fp64(const X &xa, const Tile &t, int j, double n64[S], double &ux,
+                                             double &uy, double &T, double &cap)
+{
+    using L = Lanes<typename Tile::V>;
+    double w = 0.0, wx = 0.0, wy = 0.0, we = 0.0, wd = 0.0;
+    cap = 0.0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        double sn = 0.0, sx = 0.0, sy = 0.0, se = 0.0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const double f0 = L::get(t.ld(s * Q + 4 * r, 0, 0), j), f1 = L::get(t.ld(s * Q + 4 * r + 1, 0, 0), j);
+            const double f2 = L::get(t.ld(s * Q + 4 * r + 2, 0, 0), j), f3 = L::get(t.ld(s * Q + 4 * r + 3, 0, 0), j);
+            const double rs = (f0 + f2) + (f1 + f3);
+            double rx, ry;
+            if ((r & 1) == 0) {
+                rx = f0 - f2;
+                ry = f1 - f3;
+            } else {
+                const double a = f0 - f2, b = f3 - f1;
+                rx = a + b;
+                ry = a - b;
+            }
+            sn += rs;
+            sx = fma(xa.vr[s][r], rx, sx);
+            sy = fma(xa.vr[s][r], ry, sy);
+            se = fma(xa.qr[s][r], rs, se);
+        }
+        n64[s] = sn;
+        w = fma(xa.lam[s], sn, w);
+        wx = fma(xa.lam[s], sx, wx);
+        wy = fma(xa.lam[s], sy, wy);
+        we = fma(xa.lam[s], se, we);
+        wd = fma(xa.kap[s], sn, wd);
+        cap = fma(xa.dpi[s], sn, cap);
+    }
+    ux = wx / w;
+    uy = wy / w;
+    T = (we - fma(ux, ux, uy * uy) * w) / wd;
+}
+
 // Where the cell sits and which ghost images its values must also reach.
 struct Site {
     int x, y;
@@ -424,13 +526,19 @@ static_assert(dir_x(0) == 1 && dir_y(1) == 1 && dir_x(2) == -1 && dir_y(3) == -1
 // single-problem kernels pass the same parameter block twice; the batched
 // kernel passes the launch's shared constants as `c`, so that they stay
 // constant-bank operands, and each instance's own block as `g`.
-template <int S, class K, class G, class Tile, class Out>
+template <int S, class K, class G, class Tile, class Out, class X = NoAcc>
 __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t, int x, int y, bool two,
-                                          const Out &out, unsigned *__restrict__ flag)
+                                          const Out &out, unsigned *__restrict__ flag, const X &xa = X{})
 {
     using V = typename Tile::V;
     using L = Lanes<V>;
     static_assert(L::n == 1 || Out::kNoImages, "ghost images are written one cell per thread");
+    // arithmetic options (AccConsts): run-time switches of the option kernel
+    bool t64 = false, sr = false;
+    if constexpr (X::on) {
+        t64 = xa.thermo64 != 0;
+        sr = xa.stochastic != 0;
+    }
 
     // 1. species moments, by ring sums
     V n[S], nf = bc<V>(0.0f), no = bc<V>(0.0f), cap, w, wx, wy, we, wd;
@@ -483,10 +591,31 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
     V rw, T;
 #pragma unroll
     for (int j = 0; j < L::n; ++j) L::set(rw, j, 1.0f / L::get(w, j));
-    const V ux = vmul(wx, rw), uy = vmul(wy, rw);
+    V ux = vmul(wx, rw), uy = vmul(wy, rw);
 #pragma unroll
     for (int j = 0; j < L::n; ++j)
         L::set(T, j, mixture_T(L::get(we, j), L::get(w, j), L::get(wd, j), L::get(ux, j), L::get(uy, j)));
+    // DBM_THERMO_FP64: n^s, u and T from double sums replace the float ones
+    double n64[S][L::n], T64[L::n], cap64[L::n], om64[L::n], dT64[L::n];
+    if constexpr (X::on) {
+        if (t64) {
+#pragma unroll
+            for (int j = 0; j < L::n; ++j) {
+                double nl[S], u0, u1, Tj, cp;
+                moments_fp64<S>(xa, t, j, nl, u0, u1, Tj, cp);
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    n64[s][j] = nl[s];
+                    L::set(n[s], j, __double2float_rn(nl[s]));
+                }
+                T64[j] = Tj;
+                cap64[j] = cp;
+                L::set(ux, j, __double2float_rn(u0));
+                L::set(uy, j, __double2float_rn(u1));
+                L::set(T, j, __double2float_rn(Tj));
+            }
+        }
+    }
 
     unsigned bad = 0;
     V a;  // sum_s |n^s|
@@ -508,7 +637,23 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
 
     // 3. reaction: omega_ov and T' (state after a time tau^s)
     V om = bc<V>(0.0f), dT = bc<V>(0.0f);
-    if (g.has_reaction) {
+    if constexpr (X::on) {
+        if (t64 && g.has_reaction) {  // the Arrhenius rate and T' in double
+#pragma unroll
+            for (int j = 0; j < L::n; ++j) {
+                double nF = 0.0, nO = 0.0;
+#pragma unroll
+                for (int s = 0; s < S; ++s) {
+                    if (s == g.fuel) nF = n64[s][j];
+                    if (s == g.oxid) nO = n64[s][j];
+                }
+                const double Tj = T64[j];
+                om64[j] = xa.k_ov * nF * nO * exp(-xa.Ea_over_R / Tj);
+                dT64[j] = (xa.Qheat - 0.5 * Tj * xa.src) * om64[j] / (0.5 * cap64[j]);
+            }
+        }
+    }
+    if (g.has_reaction && !t64) {
 #pragma unroll
         for (int j = 0; j < L::n; ++j) {
             const float Tj = L::get(T, j);
@@ -530,6 +675,11 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
     w_.cell = (long long)(y + GY) * g.pitch + (x + GX);
     const bool images = kImages && (w_.mx | w_.my) != 0u;
     out.put_mix(w_, ux, uy, T);
+    unsigned hcell[L::n];  // per-cell hash of the stochastic rounding
+    if constexpr (X::on) {
+#pragma unroll
+        for (int j = 0; j < L::n; ++j) hcell[j] = mix32((unsigned)(y * g.nx + x + j) * 0x9e3779b9u ^ xa.seed);
+    }
 
     // the species loop is unrolled up to three species: the constants of each
     // species then index the constant bank directly (measured 6-8 % faster
@@ -552,10 +702,35 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
             V nr = ns, Ts = T;
             if (g.has_reaction) {
                 nr = vfma(bc<V>(g.tau_a[s]), om, ns);
+                Ts = vfma(bc<V>(g.tau_d[s]), dT, T);
+                if constexpr (X::on) {
+                    if (t64 || sr) {
+#pragma unroll
+                        for (int j = 0; j < L::n; ++j) {
+                            double nd, Td;
+                            if (t64) {
+                                double n_s = 0.0;
+#pragma unroll
+                                for (int q = 0; q < S; ++q)
+                                    if (q == s) n_s = n64[q][j];
+                                nd = fma(xa.tau_a[s], om64[j], n_s);
+                                Td = fma(xa.tau_d[s], dT64[j], T64[j]);
+                            } else {  // n + tau a omega exactly (the product of two floats is exact in double)
+                                nd = fma((double)g.tau_a[s], (double)L::get(om, j), (double)L::get(ns, j));
+                                Td = fma((double)g.tau_d[s], (double)L::get(dT, j), (double)L::get(T, j));
+                            }
+                            L::set(nr, j, sr ? sr_round(nd, sr_uniform(hcell[j], S * Q + 1 + s))
+                                             : __double2float_rn(nd));
+                            if (sr)
+                                L::set(Ts, j, sr_round(Td, sr_uniform(hcell[j], S * Q + 1 + S + s)));
+                            else if (t64)
+                                L::set(Ts, j, __double2float_rn(Td));
+                        }
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < L::n; ++j)
                     if ((j == 0 || two) && L::get(nr, j) < -1e-6f * L::get(a, j)) bad |= DBM_HEALTH_NSTAR;
-                Ts = vfma(bc<V>(g.tau_d[s]), dT, T);
             }
             fhat_blocks<V>(nr, ux, uy, vmul(Ts, bc<V>(c.inv_m[s])), c.dpi[s], cb);
             bool present = false;  // an absent species feels no force
@@ -596,7 +771,14 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
             }
         }
         V o[16];
-        solve_blocks<V>(c, s, cb, o);
+        bool done = false;
+        if constexpr (X::on) {
+            if (sr) {
+                solve_blocks<V, K, true>(c, s, cb, o, hcell, S * Q + 1 + 2 * S + 4 * s);
+                done = true;
+            }
+        }
+        if (!done) solve_blocks<V>(c, s, cb, o);
         const V dtt = bc<V>(c.dt_tau[s]);
 
 #pragma unroll
@@ -606,6 +788,29 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
             // with the 5. NND advection terms of x and y each applied as one
             // fused multiply-add (no product is left for the compiler to fuse)
             const V e = feq_of<V>(i, o);
+            if constexpr (X::on) {
+                if (sr) {  // the increment, then one stochastically rounded sum
+                    V d = vmul(dtt, vsub(e, f0[i]));
+                    if (dir_x(i) > 0)
+                        d = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos<V>(t.ld(p, -2, 0), t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0)),
+                                 d);
+                    else if (dir_x(i) < 0)
+                        d = vfma(bc<V>(c.cdx[s][r]), nnd_diff_neg<V>(t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0), t.ld(p, 2, 0)),
+                                 d);
+                    if (dir_y(i) > 0)
+                        d = vfma(bc<V>(-c.cdy[s][r]), nnd_diff_pos<V>(t.ld(p, 0, -2), t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1)),
+                                 d);
+                    else if (dir_y(i) < 0)
+                        d = vfma(bc<V>(c.cdy[s][r]), nnd_diff_neg<V>(t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1), t.ld(p, 0, 2)),
+                                 d);
+                    V f1;
+#pragma unroll
+                    for (int j = 0; j < L::n; ++j)
+                        L::set(f1, j, sr_add(L::get(f0[i], j), L::get(d, j), sr_uniform(hcell[j], p + 1)));
+                    out.put(w_, p, f1, e);
+                    continue;
+                }
+            }
             V f1 = vfma(dtt, vsub(e, f0[i]), f0[i]);
             if (dir_x(i) > 0)
                 f1 = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos<V>(t.ld(p, -2, 0), t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0)),
@@ -676,7 +881,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long lo
     return false;
 }
 
-constexpr long long TMA_WAIT_LIMIT = 1LL << 22;  // try_wait polls (each may suspend ~us)
+constexpr long long TMA_WAIT_LIMIT = TMA_WAIT_POLLS;  // drain wait: try_wait polls (each may suspend ~us)
 
 // Issue the tile copy (leader thread): box origin column bx0 (= bx0 + GX - 4),
 // row by0 (= by0 + GY - 2), plane 0.
@@ -691,6 +896,15 @@ __device__ __forceinline__ void tma_tile_load(float *tile, unsigned long long tm
         : "memory");
 }
 
+// Source index of ghost index g (one of -2, -1, n, n + 1) on an axis of n
+// cells: the periodic image or the outflow edge cell.
+__device__ __forceinline__ int halo_source(int g, int n, int bc)
+{
+    if (bc != DBM_BC_PERIODIC) return min(max(g, 0), n - 1);
+    if (n >= 2) return g < 0 ? g + n : g - n;
+    return 0;  // one cell: every image is that cell
+}
+
 // Halo of a tile that touches the domain boundary, taken from the interior
 // of the input state (periodic: the wrapped cells; outflow: the edge cell)
 // instead of from stored ghost cells.  The tile holds global columns
@@ -698,6 +912,8 @@ __device__ __forceinline__ void tma_tile_load(float *tile, unsigned long long tm
 // cross-shaped stencil reaches into the halo, so the x halo is needed in the
 // tile's interior rows and the y halo in its interior columns.  All threads
 // of the CTA call this (it ends with a barrier when it wrote anything).
+// The work items of each side are (plane, row or column, ghost index) with
+// compile-time extents, so no division by a run-time value is needed.
 template <int NP, int TX, int TY>
 __device__ __forceinline__ void fill_tile_halo(float *tile, const float *__restrict__ fin, int bx0, int by0, int nx,
                                                int ny, int pitch, long long plane, int bc_x, int bc_y, int tid,
@@ -710,38 +926,46 @@ __device__ __forceinline__ void fill_tile_halo(float *tile, const float *__restr
     // ny+1} inside those ranges are filled (tile column = x - bx0 + 4 stays
     // within 2 .. TX+5, tile row = y - by0 + 2 within 0 .. TY+3)
     const int x_hi = min(bx0 + TX, nx), y_hi = min(by0 + TY, ny);
-    const int left = bx0 == 0 ? 2 : 0, right = min(max(x_hi - nx + 2, 0), 2);
-    const int top = by0 == 0 ? 2 : 0, bottom = min(max(y_hi - ny + 2, 0), 2);
-    if (left + right + top + bottom == 0) return;  // uniform over the CTA
-    // x halo, rows by0 .. y_hi-1
-    const int ncx = left + right, rows = y_hi - by0;
-    const int nxi = ncx * rows * NP;
-    for (int it = tid; it < nxi; it += nthr) {
-        const int cidx = it % ncx, r = (it / ncx) % rows, p = it / (ncx * rows);
-        const int xg = cidx < left ? cidx - 2 : nx + (cidx - left);
-        const int xs = bc_x == DBM_BC_PERIODIC ? ((xg % nx) + nx) % nx : min(max(xg, 0), nx - 1);
-        const int y = by0 + r;
-        tile[p * PS + (y - by0 + 2) * BX + (xg - bx0 + 4)] =
-            fin[(long long)p * plane + (long long)(y + GY) * pitch + (xs + GX)];
+    const bool left = bx0 == 0, top = by0 == 0;
+    const int right = min(max(x_hi - nx + 2, 0), 2), bottom = min(max(y_hi - ny + 2, 0), 2);
+    if (!left && !top && right + bottom == 0) return;  // uniform over the CTA
+    const long long base = (long long)GY * pitch + GX;
+    // x halo: rows by0 .. y_hi-1; item = (plane, row, ghost column j of 2)
+    for (int side = 0; side < 2; ++side) {
+        const int need = side == 0 ? (left ? 2 : 0) : right;
+        if (need == 0) continue;
+        for (int it = tid; it < 2 * TY * NP; it += nthr) {
+            const int j = it & 1, r = (it >> 1) % TY, p = (it >> 1) / TY;
+            const int y = by0 + r;
+            if (j >= need || y >= y_hi) continue;
+            const int xg = side == 0 ? j - 2 : nx + j;
+            const int xs = halo_source(xg, nx, bc_x);
+            tile[p * PS + (r + 2) * BX + (xg - bx0 + 4)] = fin[p * plane + base + (long long)y * pitch + xs];
+        }
     }
-    // y halo, columns bx0 .. x_hi-1
-    const int nry = top + bottom, cols = x_hi - bx0;
-    const int nyi = nry * cols * NP;
-    for (int it = tid; it < nyi; it += nthr) {
-        const int c = it % cols, ridx = (it / cols) % nry, p = it / (cols * nry);
-        const int yg = ridx < top ? ridx - 2 : ny + (ridx - top);
-        const int ys = bc_y == DBM_BC_PERIODIC ? ((yg % ny) + ny) % ny : min(max(yg, 0), ny - 1);
-        const int x = bx0 + c;
-        tile[p * PS + (yg - by0 + 2) * BX + (x - bx0 + 4)] =
-            fin[(long long)p * plane + (long long)(ys + GY) * pitch + (x + GX)];
+    // y halo: columns bx0 .. x_hi-1; item = (plane, ghost row j of 2, column)
+    for (int side = 0; side < 2; ++side) {
+        const int need = side == 0 ? (top ? 2 : 0) : bottom;
+        if (need == 0) continue;
+        for (int it = tid; it < 2 * TX * NP; it += nthr) {
+            const int c = it % TX, j = (it / TX) & 1, p = it / (2 * TX);
+            const int x = bx0 + c;
+            if (j >= need || x >= x_hi) continue;
+            const int yg = side == 0 ? j - 2 : ny + j;
+            const int ys = halo_source(yg, ny, bc_y);
+            tile[p * PS + (yg - by0 + 2) * BX + (c + 4)] = fin[p * plane + base + (long long)ys * pitch + x];
+        }
     }
     __syncthreads();
 }
 
-template <int S, int TX, int TY, int CW>
+// X: NoAcc for the default arithmetic, AccConsts<S> for the kernel with the
+// thermo and rounding options.
+template <int S, int TX, int TY, int CW, class X>
 __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
     k_step_tma(const __grid_constant__ StepConsts<float, S> c, const __grid_constant__ CUtensorMap tmap,
-               const float *__restrict__ fin, float *__restrict__ fout, unsigned *__restrict__ flag)
+               const float *__restrict__ fin, float *__restrict__ fout, unsigned *__restrict__ flag,
+               const __grid_constant__ X xa)
 {
     static_assert(CW == 1 || CW == 2, "one or two cells per thread");
     constexpr int BX = TX + 8, BY = TY + 4, NP = S * Q, NT = TX / CW * TY;
@@ -759,7 +983,7 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
     }
     __syncthreads();
     if (leader) tma_tile_load(tile, reinterpret_cast<unsigned long long>(&tmap), bx0, by0, b, BYTES);
-    const bool ok = mbar_wait(b, 0, TMA_WAIT_LIMIT);
+    const bool ok = mbar_wait(b, 0, c.wait_polls);
     if (__syncthreads_or(!ok)) {
         // the copy did not land: report, give it one more bounded wait so
         // that no copy is left writing into this block's shared memory, and
@@ -776,10 +1000,10 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
     const float *base = tile + (ty + 2) * BX + (CW * tx + 4);
     if constexpr (CW == 2) {
         const SmemTile2 t{base, BY * BX, BX};
-        step_cell<S>(c, c, t, x, y, x + 1 < c.nx, o, flag);
+        step_cell<S>(c, c, t, x, y, x + 1 < c.nx, o, flag, xa);
     } else {
         const SmemTile t{base, BY * BX, BX};
-        step_cell<S>(c, c, t, x, y, true, o, flag);
+        step_cell<S>(c, c, t, x, y, true, o, flag, xa);
     }
 }
 
@@ -794,23 +1018,27 @@ int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st)
     return set_cuda_error(h, cudaGetLastError(), "step kernel launch");
 }
 
-template <int S, int TX, int TY, int CW>
+// ACC: the kernel with the thermo and rounding options (AccConsts).
+template <int S, int TX, int TY, int CW, bool ACC>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st)
 {
+    using X = typename std::conditional<ACC, AccConsts<S>, NoAcc>::type;
     constexpr size_t smem = (size_t)(TX + 8) * (TY + 4) * S * Q * sizeof(float);
     static bool attr_set = false;  // per instantiation, set once per process
     if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_step_tma<S, TX, TY, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_step_tma<S, TX, TY, CW, X>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return set_cuda_error(h, e, "TMA step kernel shared-memory attribute");
         attr_set = true;
     }
     StepConsts<float, S> c;
     fill_step_consts<float, S>(h, c);
+    X xa{};
+    if constexpr (ACC) fill_acc_consts<S>(h, c, xa);
     dim3 block(TX / CW, TY);
     dim3 grid((h->p.nx + TX - 1) / TX, (h->p.ny + TY - 1) / TY);
-    k_step_tma<S, TX, TY, CW><<<grid, block, smem, st>>>(c, *tmap, (const float *)fin, (float *)fout,
-                                                           (unsigned *)h->scratch);
+    k_step_tma<S, TX, TY, CW, X><<<grid, block, smem, st>>>(c, *tmap, (const float *)fin, (float *)fout,
+                                                              (unsigned *)h->scratch, xa);
     return set_cuda_error(h, cudaGetLastError(), "TMA step kernel launch");
 }
 

@@ -35,6 +35,8 @@ ERRORS = {
     -8: "DBM_ERR_TIMEOUT",
 }
 KERNELS = {"auto": 0, "generic": 1, "tma": 2, "tma_cell": 3, "tma_pair": 4}
+THERMO = {"floatfloat": 0, "fp64": 1}
+ROUNDING = {"nearest": 0, "stochastic": 1}
 EXPORTS = [
     "dbm_init", "dbm_init_error", "dbm_equilibrium_matrix", "dbm_get_layout", "dbm_state_bytes", "dbm_scratch_bytes",
     "dbm_bind", "dbm_set_state", "dbm_set_f", "dbm_get_f", "dbm_step", "dbm_moments",
@@ -81,6 +83,9 @@ class dbm_params(C.Structure):
         ("accel", C.c_double * 2),
         ("precision", C.c_int),
         ("step_kernel", C.c_int),
+        ("wait_polls", C.c_int),
+        ("thermo", C.c_int),
+        ("rounding", C.c_int),
         ("sp", dbm_species * MAX_SPECIES),
     ]
 
@@ -154,7 +159,7 @@ def load(path: str = LIB_PATH):
 
 def make_params(nx, ny, species, *, dx, dy, dt, bc_x=PERIODIC, bc_y=PERIODIC, fuel=0, oxid=1,
                 k_ov=0.0, Ea_over_R=0.0, Q=0.0, accel=(0.0, 0.0), precision=FP64,
-                step_kernel="auto") -> dbm_params:
+                step_kernel="auto", wait_polls=0, thermo="floatfloat", rounding="nearest") -> dbm_params:
     """Fill a dbm_params record; ``species`` items need m, I, tau, v, eta, a."""
     if len(species) > MAX_SPECIES:
         raise ValueError(f"at most {MAX_SPECIES} species")
@@ -171,6 +176,11 @@ def make_params(nx, ny, species, *, dx, dy, dt, bc_x=PERIODIC, bc_y=PERIODIC, fu
         raise ValueError(f"step_kernel {step_kernel!r}: one of {sorted(KERNELS)}")
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.step_kernel = KERNELS[step_kernel] if isinstance(step_kernel, str) else int(step_kernel)
+    p.wait_polls = int(wait_polls)
+    for name, val, table in (("thermo", thermo, THERMO), ("rounding", rounding, ROUNDING)):
+        if isinstance(val, str) and val not in table:
+            raise ValueError(f"{name} {val!r}: one of {sorted(table)}")
+        setattr(p, name, table[val] if isinstance(val, str) else int(val))
     for s, sp in enumerate(species):
         c = p.sp[s]
         c.m, c.I, c.tau, c.a_stoich = float(sp.m), float(sp.I), float(sp.tau), float(sp.a)
@@ -180,11 +190,11 @@ def make_params(nx, ny, species, *, dx, dy, dt, bc_x=PERIODIC, bc_y=PERIODIC, fu
     return p
 
 
-def params_from_problem(pb, precision=FP64, step_kernel="auto") -> dbm_params:
+def params_from_problem(pb, precision=FP64, step_kernel="auto", **opts) -> dbm_params:
     return make_params(pb.nx, pb.ny, pb.species, dx=pb.dx, dy=pb.dy, dt=pb.dt, bc_x=pb.bc_x,
                        bc_y=pb.bc_y, fuel=pb.fuel, oxid=pb.oxid, k_ov=pb.k_ov,
                        Ea_over_R=pb.Ea_over_R, Q=pb.Q, accel=pb.accel, precision=precision,
-                       step_kernel=step_kernel)
+                       step_kernel=step_kernel, **opts)
 
 
 # ---------------------------------------------------------------------------
@@ -302,13 +312,14 @@ class Solver:
     """One DBM problem on one GPU: the handle, two state buffers and the
     scratch buffer (torch allocations), and FP64 field transfers."""
 
-    def __init__(self, problem, precision="fp64", device="cuda", stream=None, step_kernel="auto"):
+    def __init__(self, problem, precision="fp64", device="cuda", stream=None, step_kernel="auto", **opts):
+        """``opts`` are further dbm_params fields (make_params keywords)."""
         import torch
 
         self.torch = torch
         self.pb = problem
         self.device = torch.device(device)
-        self.params = params_from_problem(problem, precision, step_kernel)
+        self.params = params_from_problem(problem, precision, step_kernel, **opts)
         self.h = dbm_init(self.params)
         self.layout = dbm_get_layout(self.h)
         nb = dbm_state_bytes(self.h)

@@ -21,6 +21,9 @@ Requests (``workloads.RequestSpec``) arrive over time.  The server
   final state) into pinned host memory; the request's latency runs from its
   arrival to the moment that copy has completed.
 
+``run_sequential`` is the baseline: the same requests solved first come,
+first served, one at a time, in FP64 or FP32.
+
 Every batch of a group uses the same kernel configuration (tile shape,
 launch form, L2 promotion), so a request's result does not depend on which
 other requests it was served with.
@@ -284,6 +287,39 @@ class Server:
         return results
 
 
+def run_sequential(specs: List[W.RequestSpec], precision: str = "fp64", device="cuda",
+                   keep_f: bool = False) -> List[Result]:
+    """The baseline of continuous batching: first come, first served, one
+    request at a time, each a plain single-problem solve (``Solver``, one
+    step launch per time step) in ``precision``.  Arrival times are
+    honoured: a request that arrives while another runs waits for it.  Each
+    request's latency runs from its arrival to the moment its conserved
+    totals (and, with ``keep_f``, its final state) are in host memory."""
+    import torch
+
+    dev = torch.device(device)
+    stream = torch.cuda.Stream(device=dev)
+    results: List[Result] = []
+    t0 = time.perf_counter()
+    for spec in sorted(specs, key=lambda q: q.arrival):
+        wait = spec.arrival - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        admitted = time.perf_counter() - t0
+        with torch.cuda.stream(stream):
+            s = D.Solver(W.request_problem(spec), precision, device=dev)
+            s.set_state(*W.request_fields(spec, dev))
+            s.step(spec.nsteps)
+            cons = s.conservation().cpu().numpy()
+            f = s.get_f().cpu().numpy() if keep_f else None
+            status = s.status()[0]
+        finished = time.perf_counter() - t0
+        s.close()
+        results.append(Result(rid=spec.rid, ns=spec.ns, cells=spec.cells, nsteps=spec.nsteps, arrival=spec.arrival,
+                              admitted=admitted, finished=finished, status=status, conservation=cons, f=f))
+    return results
+
+
 def summarize(results: List[Result]) -> dict:
     """Latency percentiles and throughput (species-cell updates per second
     from the first arrival to the last completion)."""
@@ -297,9 +333,9 @@ def summarize(results: List[Result]) -> dict:
 
 
 def simulate_sequential(specs: List[W.RequestSpec], rate_by_ns: Dict[int, float]) -> dict:
-    """First-come-first-served, one request at a time, each taking
-    units / rate(S) seconds: the latencies of sequential solves with the
-    given per-species-count throughputs (species-cell updates per second)."""
+    """An extrapolation, not a run: first come, first served, one request at
+    a time, each taking units / rate(S) seconds, for mixes too large to solve
+    sequentially in the time at hand (``run_sequential`` solves them)."""
     t = 0.0
     lat = []
     units = 0

@@ -213,3 +213,55 @@ def test_bf16dev_scope(D):
         with pytest.raises(D.DbmError) as e:
             D.dbm_init(D.params_from_problem(bad, "bf16dev"))
         assert "BF16DEV" in str(e.value)
+
+
+def test_struct_layout_matches_the_header(D, tmp_path):
+    """The binding's ctypes records have the size and field offsets that a
+    C compiler gives the structs of include/dbm.h."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    fields = [name for name, _ in D.dbm_params._fields_]
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dbm.h"', "int main(void) {",
+             '  printf("params %zu\\n", sizeof(dbm_params));',
+             '  printf("layout %zu\\n", sizeof(dbm_layout));',
+             '  printf("species %zu\\n", sizeof(dbm_species));']
+    for f in fields:
+        lines.append(f'  printf("{f} %zu\\n", offsetof(dbm_params, {f}));')
+    lines.append("  return 0; }")
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    assert int(out["params"]) == ctypes.sizeof(D.dbm_params)
+    assert int(out["layout"]) == ctypes.sizeof(D.dbm_layout)
+    assert int(out["species"]) == ctypes.sizeof(D.dbm_species)
+    for f in fields:
+        assert int(out[f]) == getattr(D.dbm_params, f).offset, f
+
+
+def test_arithmetic_options_scope(D):
+    """The thermo and rounding options exist for the TMA-staged FP32 step
+    with up to 4 species; elsewhere, and for unknown values, init refuses."""
+    pb2, pb5 = W.random_smooth(8, 8, 2), W.random_smooth(8, 8, 5)
+    ok = D.dbm_init(D.params_from_problem(pb2, "fp32", thermo="fp64", rounding="stochastic"))
+    D.dbm_destroy(ok)
+    for pb, prec, kern, opts in ((pb2, "fp64", "auto", dict(thermo="fp64")),
+                                 (pb2, "bf16dev", "auto", dict(rounding="stochastic")),
+                                 (pb5, "fp32", "auto", dict(thermo="fp64")),
+                                 (pb2, "fp32", "generic", dict(rounding="stochastic")),
+                                 (pb2, "fp32", "auto", dict(thermo=7)),
+                                 (pb2, "fp32", "auto", dict(rounding=-1))):
+        with pytest.raises(D.DbmError) as e:
+            D.dbm_init(D.params_from_problem(pb, prec, kern, **opts))
+        assert e.value.code == -1, (prec, kern, opts)
+    with pytest.raises(ValueError):
+        D.params_from_problem(pb2, "fp32", thermo="fp128")
+    with pytest.raises(ValueError):
+        D.params_from_problem(pb2, "fp32", rounding="up")

@@ -335,10 +335,10 @@ def _windows(nx, ny, rng, k=4, w=24):
     return out
 
 
-@pytest.mark.parametrize("which", ["kh4096", "reactive1024"])
-def test_full_size_one_step_sampled(D, orc, which):
+@pytest.mark.parametrize("which,prec", [("kh4096", "fp32"), ("reactive1024", "fp32"), ("reactive1024", "fp64")])
+def test_full_size_one_step_sampled(D, orc, which, prec):
     pb = W.kh_shear_layer(4096) if which == "kh4096" else W.reactive_premixed()
-    s = D.Solver(pb, "fp32")
+    s = D.Solver(pb, prec)
     s.set_state()
     f0 = s.get_f()
     s.step(1)
@@ -352,7 +352,7 @@ def test_full_size_one_step_sampled(D, orc, which):
     for (x0, x1, y0, y1) in _windows(pb.nx, pb.ny, rng):
         want, st = orc.step_region(p, f0n, x0, x1, y0, y1)
         got = f1n[:, :, y0:y1, x0:x1]
-        assert rel_linf(got, want) <= 1e-6, (x0, y0)
+        assert rel_linf(got, want) <= (1e-12 if prec == "fp64" else 1e-6), (x0, y0)
 
 
 @pytest.mark.parametrize("nx,ny,ns,bc", [(130, 19, 1, (W.PERIODIC, W.PERIODIC)),

@@ -91,3 +91,47 @@ def test_zero_step_request_returns_its_initial_state(S):
     s = D.Solver(W.request_problem(spec), "fp32")
     s.set_state(*W.request_fields(spec, "cuda"))
     np.testing.assert_array_equal(r.f, s.get_f().cpu().numpy())
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _oracle_final(orc, spec):
+    pb = W.request_problem(spec)
+    rho_s, ux, uy, T = (t.numpy() for t in W.request_fields(spec, "cpu"))
+    p = orc.params_of(pb)
+    fr, st = orc.run(p, orc.init_feq(p, rho_s, ux, uy, T), spec.nsteps)
+    assert st == 0
+    return fr
+
+
+def test_served_results_match_the_oracle(S, orc):
+    """Every request of a mix served with continuous batching (shock tubes
+    and reactive gases, two to four species, arriving while others run)
+    against the FP64 oracle's solve of the same request, at the FP32 bound
+    of the parity tests (relative L-inf 2e-5 on f)."""
+    specs = [W.RequestSpec(rid=0, kind="shock", L=40, ns=2, seed=11, nsteps=30, arrival=0.0),
+             W.RequestSpec(rid=1, kind="reactive", L=36, ns=3, seed=12, nsteps=40, arrival=0.0),
+             W.RequestSpec(rid=2, kind="reactive", L=33, ns=4, seed=13, nsteps=25, arrival=0.01),
+             W.RequestSpec(rid=3, kind="reactive", L=44, ns=2, seed=14, nsteps=35, arrival=0.02),
+             W.RequestSpec(rid=4, kind="shock", L=30, ns=3, seed=15, nsteps=20, arrival=0.03),
+             W.RequestSpec(rid=5, kind="shock", L=34, ns=4, seed=16, nsteps=33, arrival=0.03)]
+    srv = S.Server(qmax=8, keep_f=True, hbm_budget=1 << 32)
+    res = {r.rid: r for r in srv.run(specs)}
+    assert sorted(res) == [q.rid for q in specs]
+    for spec in specs:
+        assert res[spec.rid].status == 0
+        err = _rel(res[spec.rid].f, _oracle_final(orc, spec))
+        assert err <= 2e-5, (spec, err)
+
+
+def test_sequential_fp64_baseline_matches_the_oracle(S, orc):
+    """The baseline the server is compared with (one request at a time,
+    plain FP64 solves) is itself held to the oracle at the FP64 bound."""
+    specs = [W.RequestSpec(rid=0, kind="reactive", L=30, ns=3, seed=21, nsteps=15),
+             W.RequestSpec(rid=1, kind="shock", L=26, ns=2, seed=22, nsteps=12)]
+    res = {r.rid: r for r in S.run_sequential(specs, "fp64", keep_f=True)}
+    for spec in specs:
+        assert res[spec.rid].status == 0
+        assert _rel(res[spec.rid].f, _oracle_final(orc, spec)) <= 1e-12
