@@ -672,7 +672,7 @@ def main():
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "kernel": step_kernel_name(pb, args.precision, solver) if args.workload != "batched"
-                else f"k_step_batch<{pb.ns},{cfg['tile'][0]},{cfg['tile'][1]}>",
+                else f"k_step_batch<{pb.ns},{cfg['tile'][0]},{cfg['tile'][1]},{cfg['batch_config']['cells']}>",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "median_launch_ms": statistics.median(per_launch)}
 

@@ -289,7 +289,7 @@ int dbm_batch_create(dbm_handle *const *handles, int n, void *table, size_t tabl
                      dbm_batch **out);
 
 /* Choose the tile shape (32x10, 32x8, 32x16, 32x7 or 64x4 cells at one cell
- * per thread, or 64x8 cells at two adjacent cells per thread), the launch form (as
+ * per thread, or 64x8 or 32x16 cells at two adjacent cells per thread), the launch form (as
  * many CTAs as are resident at once, each walking a contiguous range of
  * tiles, or one CTA per tile) and whether the tile copies promote L2 fills
  * to 256 bytes, whichever step this batch fastest: each choice is timed on
@@ -304,19 +304,22 @@ int dbm_batch_step(dbm_batch *b, int nsteps, void *stream);
 /* Current tile shape, number of tiles per step and CTAs per launch. */
 int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int *ctas);
 
-/* The batch's kernel configuration: tile shape, launch form (1: at most
- * the CTAs resident at once, each over a contiguous range of tiles; 0: one
- * CTA per tile) and L2 promotion of the tile copies (1: 256 B; 0: none).
- * Null outputs are skipped. */
-int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote);
+/* The batch's kernel configuration: tile shape and cells per thread (1,
+ * or 2 adjacent cells of a row in packed FP32x2 arithmetic), launch form
+ * (1: at most the CTAs resident at once, each over a contiguous range of
+ * tiles; 0: one CTA per tile) and L2 promotion of the tile copies (1: 256 B;
+ * 0: none).  Null outputs are skipped. */
+int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *cells_per_thread, int *persistent,
+                         int *promote);
 
-/* Set the configuration (a compiled tile shape: 32x10, 32x8, 32x16,
- * 32x7, 64x4 or 64x8), rewriting the batch's tables; synchronises the
- * stream.  Every shape runs the same explicitly rounded arithmetic as
- * dbm_step, so an instance's result is bitwise the same whatever the shape
- * and whatever else the batch holds.  DBM_ERR_INVALID for a shape that is
- * not compiled. */
-int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, void *stream);
+/* Set the configuration (a compiled shape: 32x10, 32x8, 32x16, 32x7 or
+ * 64x4 at one cell per thread, 64x8 or 32x16 at two), rewriting the batch's
+ * tables; synchronises the stream.  Every shape runs the same explicitly
+ * rounded arithmetic as dbm_step, so an instance's result is bitwise the
+ * same whatever the shape and whatever else the batch holds.
+ * DBM_ERR_INVALID for a shape that is not compiled. */
+int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int cells_per_thread, int persistent, int promote,
+                         void *stream);
 
 const char *dbm_batch_last_error(const dbm_batch *b);
 void dbm_batch_destroy(dbm_batch *b);

@@ -145,8 +145,8 @@ def load(path: str = LIB_PATH):
     L.dbm_batch_tune.argtypes = [vp, vp, C.c_int]
     L.dbm_batch_step.argtypes = [vp, C.c_int, vp]
     L.dbm_batch_info.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
-    L.dbm_batch_get_config.argtypes = [vp] + [C.POINTER(C.c_int)] * 4
-    L.dbm_batch_set_config.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp]
+    L.dbm_batch_get_config.argtypes = [vp] + [C.POINTER(C.c_int)] * 5
+    L.dbm_batch_set_config.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp]
     L.dbm_batch_last_error.argtypes = [vp]
     L.dbm_batch_last_error.restype = C.c_char_p
     L.dbm_batch_destroy.argtypes = [vp]
@@ -479,13 +479,14 @@ def dbm_batch_info(b) -> dict:
 
 
 def dbm_batch_get_config(b) -> dict:
-    v = [C.c_int() for _ in range(4)]
+    v = [C.c_int() for _ in range(5)]
     _bcheck(b, load().dbm_batch_get_config(b, *[C.byref(x) for x in v]))
-    return {"tile": (v[0].value, v[1].value), "persistent": v[2].value, "promote": v[3].value}
+    return {"tile": (v[0].value, v[1].value), "cells": v[2].value, "persistent": v[3].value, "promote": v[4].value}
 
 
-def dbm_batch_set_config(b, tile, persistent: int, promote: int, stream: int = 0) -> None:
-    _bcheck(b, load().dbm_batch_set_config(b, int(tile[0]), int(tile[1]), int(persistent), int(promote), stream))
+def dbm_batch_set_config(b, tile, cells: int, persistent: int, promote: int, stream: int = 0) -> None:
+    _bcheck(b, load().dbm_batch_set_config(b, int(tile[0]), int(tile[1]), int(cells), int(persistent), int(promote),
+                                           stream))
 
 
 def dbm_batch_destroy(b) -> None:
@@ -519,7 +520,7 @@ class Batch:
         self._enter()
         self.b = dbm_batch_create(handles, self._tp, nb, self.stream.cuda_stream)
         if config is not None:
-            dbm_batch_set_config(self.b, config["tile"], config["persistent"], config["promote"],
+            dbm_batch_set_config(self.b, config["tile"], config.get("cells", 1), config["persistent"], config["promote"],
                                  stream=self.stream.cuda_stream)
         elif tune:
             dbm_batch_tune(self.b, self.stream.cuda_stream)

@@ -45,7 +45,7 @@ from . import workloads as W
 
 # kernel configuration of the batched groups (tile shape, launch form, L2
 # promotion): what the tuner picks for instances of 288^2 and 512^2 cells
-DEFAULT_CONFIG = {"tile": (32, 16), "persistent": 0, "promote": 1}
+DEFAULT_CONFIG = {"tile": (32, 16), "cells": 1, "persistent": 0, "promote": 1}
 
 
 class Admission:

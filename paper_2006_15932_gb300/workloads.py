@@ -175,6 +175,32 @@ def reactive_premixed(nx: int = 1024, ny: int = 256, seed: int = SEED, nsteps: i
                    nsteps=nsteps, rho_s=rho_s, ux=np.zeros((ny, nx)), uy=np.zeros((ny, nx)), T=T)
 
 
+def premixed_flame(nx: int = 300) -> Problem:
+    """A one-dimensional premixed flame (section "Flame at constant
+    pressure" in spirit; the propane chemistry is not given): three species
+    F + O -> 2 P (a = -1, -1, +2, m = 1), a high activation temperature
+    E_a/R = 16 so that the fresh gas at T = 1 is nearly inert while the burnt
+    gas at T = 1.8 reacts fast (k_ov = 1.4e6), heat Q = 8 per mole of
+    reaction; burnt products (T = 1.8, 2 % reactants left) at x < 40 meet the
+    fresh mixture (Y_F = Y_O = 0.5, T = 1) through a tanh profile of width
+    2 cells at constant pressure p = 1; tau = 2e-4 (a thick, resolved flame),
+    D2V16 ring speeds scaled for T_ref = 1.3; outflow at both ends, one row.
+    The flame propagates into the fresh gas, about 0.4 cells per thousand
+    steps."""
+    tau = 2e-4
+    sp = [species(tau=tau, a=-1.0, T_ref=1.3), species(tau=tau, a=-1.0, T_ref=1.3),
+          species(tau=tau, a=2.0, T_ref=1.3)]
+    x = np.arange(nx)[None, :].astype(np.float64)
+    burnt = 0.5 * (1.0 - np.tanh((x - 40.0) / 2.0))
+    T = 1.0 + 0.8 * burnt
+    rho = 1.0 / T
+    yF = 0.5 - 0.49 * burnt
+    rho_s = np.stack([rho * yF, rho * yF, rho * (1.0 - 2.0 * yF)])
+    return Problem(name=f"flame_{nx}", nx=nx, ny=1, species=sp, dx=1e-3, dy=1e-3, dt=1e-5, bc_x=OUTFLOW,
+                   bc_y=PERIODIC, fuel=0, oxid=1, k_ov=1.4e6, Ea_over_R=16.0, Q=8.0, nsteps=30000, rho_s=rho_s,
+                   ux=np.zeros((1, nx)), uy=np.zeros((1, nx)), T=T)
+
+
 def kh_shear_layer(n: int = 4096, seed: int = SEED, ny: int | None = None) -> Problem:
     """Kelvin-Helmholtz shear layer with the paper's geometry (section
     "Kelvin-Helmholtz instability"): two species, u_y = 0.5 tanh((x-x0)/w)

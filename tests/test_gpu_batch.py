@@ -63,6 +63,9 @@ def test_batch_tune_leaves_states_unchanged(D):
     batch = D.Batch(sols, stream=stream, tune=True)
     info = batch.info()
     assert info["tile"] in ((32, 10), (32, 8), (32, 16), (32, 7), (64, 4), (64, 8)) and info["tiles"] > 0
+    cfg = batch.config()
+    assert (cfg["tile"], cfg["cells"]) in (((32, 10), 1), ((32, 8), 1), ((32, 16), 1), ((32, 7), 1), ((64, 4), 1),
+                                           ((64, 8), 2), ((32, 16), 2))
     after = [s.get_f().cpu().numpy() for s in sols]
     for a, b in zip(before, after):
         assert np.array_equal(a, b)
@@ -117,11 +120,11 @@ def test_batch_rejects_mixed_species_or_precision(D):
             D.Batch(group, stream=stream)
 
 
-@pytest.mark.parametrize("ns,n", [(1, 70), (2, 45), (3, 33), (4, 27)])
+@pytest.mark.parametrize("ns,n", [(1, 131), (2, 130), (3, 126), (4, 124)])
 def test_batch_spanning_several_launch_chunks(D, ns, n):
-    """More instances than one launch's parameter block holds (50, 35, 27
-    and 22 instances for S = 1, 2, 3, 4): the batch runs several chunks per step;
-    every instance must still match its own single-problem steps."""
+    """More instances than one launch's parameter block holds (125, 123, 122
+    and 121 instances for S = 1, 2, 3, 4): the batch runs several chunks per
+    step; every instance must still match its own single-problem steps."""
     rng = np.random.default_rng(40 + ns)
     pbs = []
     for k in range(n):
@@ -219,3 +222,37 @@ def test_batched_workload_full_size_sampled(D, orc):
             got = f2[:, :, y0:y0 + w, x0:x0 + w]
             assert rel(got, want) <= 1e-6, (k, x0, y0)
     batch.close()
+
+
+SHAPES = [((32, 10), 1), ((32, 8), 1), ((32, 16), 1), ((32, 7), 1), ((64, 4), 1), ((64, 8), 2), ((32, 16), 2)]
+
+
+@pytest.mark.parametrize("tile,cells", SHAPES)
+def test_every_batch_shape_matches_single_problem_steps(D, tile, cells):
+    """Each compiled tile shape, one CTA per tile and persistent, gives the
+    bits of the single-problem steps on a mix of shock tubes (outflow in x)
+    and reactive gases (periodic) whose sides leave ragged tiles."""
+    pbs = _mixed(6, seed=31)
+    stream = torch.cuda.Stream()
+    solo = []
+    for pb in pbs:
+        s = D.Solver(pb, "fp32", stream=stream)
+        s.set_state()
+        s.step(5)
+        solo.append(s)
+    want = [s.get_f().cpu().numpy() for s in solo]
+    for persistent in (0, 1):
+        mixed = []
+        for pb in pbs:
+            s = D.Solver(pb, "fp32", stream=stream)
+            s.set_state()
+            mixed.append(s)
+        batch = D.Batch(mixed, stream=stream, config={"tile": tile, "cells": cells, "persistent": persistent,
+                                                      "promote": 1})
+        assert batch.config()["cells"] == cells and batch.config()["tile"] == tile
+        batch.step(5)
+        torch.cuda.synchronize()
+        for a, b in zip(want, mixed):
+            assert b.status()[0] == 0
+            assert np.array_equal(b.get_f().cpu().numpy(), a)
+        batch.close()

@@ -123,3 +123,51 @@ def test_free_falling_reactive_box(D, precision):
     assert released > 0  # the gas burned
     assert abs((c1[S + 2] + c1[S + 3]) - (c0[S + 2] + c0[S + 3])
                - 0.5 * sum(c0[:S]) * ((n * pb.dt * a) ** 2)) < 0.01 * released  # kinetic energy of the fall added
+
+
+def _flame_profile(D, s, pb):
+    """Front (last cell above the mid temperature), omega_ov, Delta_2xx of the
+    oxidiser and the total Delta_3,1x, along the one row."""
+    S = pb.ns
+    m = s.moments().cpu().numpy()[:, 0, :]
+    ne = s.nonequilibrium().cpu().numpy()[:, 0, :]
+    T = m[4 * S + 3]
+    omega = pb.k_ov * m[4 * pb.fuel] * m[4 * pb.oxid] * np.exp(-pb.Ea_over_R / T)
+    d2 = ne[20 * pb.oxid + 0]
+    d31 = sum(ne[20 * q + 3] for q in range(S))
+    front = int(np.argmax(T < 0.5 * (T.max() + T[-5])))
+    return front, omega, d2, d31, m[4 * S + 1]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_premixed_flame_nonequilibrium(D, precision):
+    """A propagating premixed flame (section "Flame at constant pressure",
+    Fig. 3, with a synthetic one-step chemistry; workloads.premixed_flame):
+    the front advances into the fresh gas; Delta_2xx of the oxidiser has its
+    trough at the front, where the gas expands (du_x/dx > 0, so the viscous
+    part -mu (2 - 2/(D+I)) du_x/dx of Delta_2xx is negative) and the trough
+    outweighs the positive lobe of the preheat zone ahead; the nonorganised
+    energy flux Delta_3,1x is positive at the front (heat carried into the
+    fresh gas); the burnt gas flows back through the open left end; the
+    reaction zone (peak of omega_ov) lies within the flame, a few cells on the
+    burnt side of the trough.  The paper's propane flame shows the omega_ov
+    peak ahead of the trough; this one-step chemistry with its heat release
+    at the hot end puts it behind."""
+    pb = W.premixed_flame()
+    s = D.Solver(pb, precision)
+    s.set_state()
+    fronts = []
+    for _ in range(3):
+        s.step(10000)
+        assert s.status()[0] == 0
+        front, omega, d2, d31, ux = _flame_profile(D, s, pb)
+        fronts.append(front)
+        trough = int(np.argmin(d2))
+        assert d2[trough] < 0 and abs(trough - front) <= 2, (front, trough)
+        assert -d2[trough] > 1.2 * np.max(d2), (d2[trough], np.max(d2))
+        assert d31[front] > 0
+        peak = int(np.argmax(omega))
+        assert front - 8 <= peak <= front, (front, peak)
+        assert ux[: front - 10].min() < 0  # the burnt gas flows out to the left
+    assert fronts[1] >= fronts[0] + 2 and fronts[2] >= fronts[1] + 2, fronts
+    s.close()
