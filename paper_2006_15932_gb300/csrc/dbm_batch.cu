@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
         const BatchTile cur = next;
         if (t + 1 < t1) next = tiles[t + 1];
         const BatchInst<S> &e = P.e[cur.k];
+        const InstConsts<S> &g = e.c;
         __syncthreads();  // barrier initialised / previous tile no longer read
         if (leader) {
             // the previous tile's halo fill and stencil reads went through the
@@ -159,7 +160,11 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
             if (t > t0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tma_tile_load(tile, reinterpret_cast<unsigned long long>(&e.tmap), cur.bx0, cur.by0, b, BYTES);
         }
-        const bool ok = mbar_wait(b, phase, e.c.wait_polls);
+        const int tid = ty * (TX / CW) + tx;
+        const HaloSides hs = halo_sides<TX, TY>(cur.bx0, cur.by0, g.nx, g.ny);
+        HaloRegs<NP, TX, TY, NT> hr;
+        if (hs.any()) halo_load(hr, hs, e.fin, cur.bx0, cur.by0, g.nx, g.ny, g.pitch, g.plane, g.bc_x, g.bc_y, tid);
+        const bool ok = mbar_wait(b, phase, g.wait_polls);
         if (__syncthreads_or(!ok)) {
             // the copy did not land: report, give it one more bounded wait so
             // that no copy is left writing into shared memory, leave together
@@ -167,9 +172,7 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
             mbar_wait(b, phase, TMA_WAIT_LIMIT);
             return;
         }
-        const InstConsts<S> &g = e.c;
-        fill_tile_halo<NP, TX, TY>(tile, e.fin, cur.bx0, cur.by0, g.nx, g.ny, g.pitch, g.plane, g.bc_x, g.bc_y,
-                                   ty * (TX / CW) + tx, NT);
+        if (hs.any()) halo_store(hr, hs, tile, cur.bx0, cur.by0, g.nx, g.ny, tid);
         const int x = cur.bx0 + CW * tx, y = cur.by0 + ty;
         if (x < g.nx && y < g.ny) {
             StateOutNoImages o{e.fout, g.plane};
@@ -212,11 +215,12 @@ typedef CUresult (*encode_tiled_fn_b)(CUtensorMap *, CUtensorMapDataType, cuuint
                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                       CUtensorMapFloatOOBfill);
 
-// Tile shapes compiled for the batched kernel (cells); the last one runs
-// two cells per thread.
-static const int N_SHAPES = 6;
-static const int SHAPE_TX[N_SHAPES] = {32, 32, 32, 32, 64, 64};
-static const int SHAPE_TY[N_SHAPES] = {10, 8, 16, 7, 4, 8};
+// Tile shapes compiled for the batched kernel (cells) and the cells each
+// thread updates (1, or 2 adjacent cells of a row in packed FP32x2).
+static const int N_SHAPES = 7;
+static const int SHAPE_TX[N_SHAPES] = {32, 32, 32, 32, 64, 64, 32};
+static const int SHAPE_TY[N_SHAPES] = {10, 8, 16, 7, 4, 8, 16};
+static const int SHAPE_CW[N_SHAPES] = {1, 1, 1, 1, 1, 2, 2};
 
 template <int S>
 static BatchKernel batch_kernel_s(int shape)
@@ -227,7 +231,8 @@ static BatchKernel batch_kernel_s(int shape)
     case 2: return batch_kernel<S, 32, 16, 1>();
     case 3: return batch_kernel<S, 32, 7, 1>();
     case 4: return batch_kernel<S, 64, 4, 1>();
-    default: return batch_kernel<S, 64, 8, 2>();
+    case 5: return batch_kernel<S, 64, 8, 2>();
+    default: return batch_kernel<S, 32, 16, 2>();
     }
 }
 
@@ -642,22 +647,25 @@ int dbm_batch_info(const dbm_batch *b, int *tile_x, int *tile_y, int *tiles, int
     return DBM_OK;
 }
 
-int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *persistent, int *promote)
+int dbm_batch_get_config(const dbm_batch *b, int *tile_x, int *tile_y, int *cells_per_thread, int *persistent,
+                         int *promote)
 {
     if (!b) return DBM_ERR_INVALID;
     if (tile_x) *tile_x = SHAPE_TX[b->shape];
     if (tile_y) *tile_y = SHAPE_TY[b->shape];
+    if (cells_per_thread) *cells_per_thread = SHAPE_CW[b->shape];
     if (persistent) *persistent = b->persistent;
     if (promote) *promote = b->promote;
     return DBM_OK;
 }
 
-int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int persistent, int promote, void *stream)
+int dbm_batch_set_config(dbm_batch *b, int tile_x, int tile_y, int cells_per_thread, int persistent, int promote,
+                         void *stream)
 {
     if (!b || (persistent != 0 && persistent != 1) || (promote != 0 && promote != 1)) return DBM_ERR_INVALID;
     int shape = -1;
     for (int sh = 0; sh < N_SHAPES; ++sh)
-        if (SHAPE_TX[sh] == tile_x && SHAPE_TY[sh] == tile_y) shape = sh;
+        if (SHAPE_TX[sh] == tile_x && SHAPE_TY[sh] == tile_y && SHAPE_CW[sh] == cells_per_thread) shape = sh;
     if (shape < 0) return bfail(b, DBM_ERR_INVALID, "tile shape not compiled for batches");
     b->shape = shape;
     b->persistent = persistent;

@@ -480,7 +480,7 @@ struct StateOut {
 
 // Output of the TMA-staged FP32 steps: f^{n+1} only, one or two cells per
 // thread.  These kernels never read the stored ghost cells (a tile at the
-// domain boundary takes its halo from the interior, fill_tile_halo), so they
+// domain boundary takes its halo from the interior, halo_fill), so they
 // do not write them either.
 struct StateOutNoImages {
     static constexpr bool kNoImages = true;
@@ -597,6 +597,11 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
         L::set(T, j, mixture_T(L::get(we, j), L::get(w, j), L::get(wd, j), L::get(ux, j), L::get(uy, j)));
     // DBM_THERMO_FP64: n^s, u and T from double sums replace the float ones
     double n64[S][L::n], T64[L::n], cap64[L::n], om64[L::n], dT64[L::n];
+    unsigned hcell[L::n];  // per-cell hash of the stochastic rounding
+    if constexpr (X::on) {
+#pragma unroll
+        for (int j = 0; j < L::n; ++j) hcell[j] = mix32((unsigned)(y * g.nx + x + j) * 0x9e3779b9u ^ xa.seed);
+    }
     if constexpr (X::on) {
         if (t64) {
 #pragma unroll
@@ -613,6 +618,23 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
                 L::set(ux, j, __double2float_rn(u0));
                 L::set(uy, j, __double2float_rn(u1));
                 L::set(T, j, __double2float_rn(Tj));
+            }
+        }
+        // stochastic rounding: the mixture T, from which every species'
+        // equilibrium energy follows, rounded without bias (the float-float
+        // numerator, or the double T, evaluated in double)
+        if (sr) {
+#pragma unroll
+            for (int j = 0; j < L::n; ++j) {
+                double Td;
+                if (t64) {
+                    Td = T64[j];
+                } else {
+                    const double u0 = L::get(ux, j), u1 = L::get(uy, j);
+                    Td = ((double)L::get(we, j) - fma(u0, u0, u1 * u1) * (double)L::get(w, j)) / (double)L::get(wd, j);
+                }
+                T64[j] = Td;
+                L::set(T, j, sr_round(Td, sr_uniform(hcell[j], 0)));
             }
         }
     }
@@ -675,11 +697,6 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
     w_.cell = (long long)(y + GY) * g.pitch + (x + GX);
     const bool images = kImages && (w_.mx | w_.my) != 0u;
     out.put_mix(w_, ux, uy, T);
-    unsigned hcell[L::n];  // per-cell hash of the stochastic rounding
-    if constexpr (X::on) {
-#pragma unroll
-        for (int j = 0; j < L::n; ++j) hcell[j] = mix32((unsigned)(y * g.nx + x + j) * 0x9e3779b9u ^ xa.seed);
-    }
 
     // the species loop is unrolled up to three species: the constants of each
     // species then index the constant bank directly (measured 6-8 % faster
@@ -733,6 +750,17 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
                     if ((j == 0 || two) && L::get(nr, j) < -1e-6f * L::get(a, j)) bad |= DBM_HEALTH_NSTAR;
             }
             fhat_blocks<V>(nr, ux, uy, vmul(Ts, bc<V>(c.inv_m[s])), c.dpi[s], cb);
+            if constexpr (X::on) {
+                if (sr) {  // the energy target n* ((D+I) T*/m + u.u) formed in double, rounded without bias
+#pragma unroll
+                    for (int j = 0; j < L::n; ++j) {
+                        const double u0 = L::get(ux, j), u1 = L::get(uy, j);
+                        const double th = (double)L::get(Ts, j) * (double)c.inv_m[s];
+                        const double e1 = (double)L::get(nr, j) * fma((double)c.dpi[s], th, fma(u0, u0, u1 * u1));
+                        L::set(cb[1], j, sr_round(e1, sr_uniform(hcell[j], S * Q + 1 + 6 * S + s)));
+                    }
+                }
+            }
             bool present = false;  // an absent species feels no force
 #pragma unroll
             for (int j = 0; j < L::n; ++j) present |= L::get(ns, j) != 0.0f;
@@ -910,50 +938,160 @@ __device__ __forceinline__ int halo_source(int g, int n, int bc)
 // instead of from stored ghost cells.  The tile holds global columns
 // bx0-4 .. bx0+TX+3 and rows by0-2 .. by0+TY+1 of all NP planes; only the
 // cross-shaped stencil reaches into the halo, so the x halo is needed in the
-// tile's interior rows and the y halo in its interior columns.  All threads
-// of the CTA call this (it ends with a barrier when it wrote anything).
-// The work items of each side are (plane, row or column, ghost index) with
-// compile-time extents, so no division by a run-time value is needed.
-template <int NP, int TX, int TY>
-__device__ __forceinline__ void fill_tile_halo(float *tile, const float *__restrict__ fin, int bx0, int by0, int nx,
-                                               int ny, int pitch, long long plane, int bc_x, int bc_y, int tid,
-                                               int nthr)
+// tile's interior rows and the y halo in its interior columns: interior
+// cells span columns bx0 .. x_hi-1 and rows by0 .. y_hi-1, their stencil
+// reads columns bx0-2 .. x_hi+1 and rows by0-2 .. y_hi+1, so only the ghost
+// columns {-2, -1, nx, nx+1} and rows {-2, -1, ny, ny+1} inside those
+// ranges are filled (tile column = x - bx0 + 4 stays within 2 .. TX+5, tile
+// row = y - by0 + 2 within 0 .. TY+3).
+//
+// The input buffer is only read by the step, so a boundary tile loads its
+// halo values into registers before it waits for its tile copy (halo_load)
+// and stores them into the tile once the copy has landed (halo_store): the
+// load latency overlaps the copy instead of following it.  Work items of a
+// side are (plane, row or column, ghost index j of 2) with compile-time
+// extents; thread tid takes items tid, tid + NT, ... into fixed registers.
+template <int NP, int TX, int TY, int NT>
+struct HaloRegs {
+    static constexpr int XI = 2 * TY * NP, YI = 2 * TX * NP;  // items of one x side, one y side
+    static constexpr int XK = (XI + NT - 1) / NT, YK = (YI + NT - 1) / NT;
+    float x[2][XK], y[2][YK];
+};
+
+// Which ghost layers a tile needs: 2 columns left, `right` (0..2) columns
+// right, 2 rows on top, `bottom` rows at the bottom; false for an interior
+// tile (uniform over the CTA).
+struct HaloSides {
+    int left, right, top, bottom, x_hi, y_hi;
+    __device__ __forceinline__ bool any() const { return left + right + top + bottom != 0; }
+};
+
+template <int TX, int TY>
+__device__ __forceinline__ HaloSides halo_sides(int bx0, int by0, int nx, int ny)
 {
-    constexpr int BX = TX + 8, PS = (TY + 4) * BX;
-    // interior cells of the tile: columns bx0 .. x_hi-1, rows by0 .. y_hi-1;
-    // their stencil reads columns bx0-2 .. x_hi+1 and rows by0-2 .. y_hi+1,
-    // so only the ghost columns {-2, -1, nx, nx+1} and rows {-2, -1, ny,
-    // ny+1} inside those ranges are filled (tile column = x - bx0 + 4 stays
-    // within 2 .. TX+5, tile row = y - by0 + 2 within 0 .. TY+3)
-    const int x_hi = min(bx0 + TX, nx), y_hi = min(by0 + TY, ny);
-    const bool left = bx0 == 0, top = by0 == 0;
-    const int right = min(max(x_hi - nx + 2, 0), 2), bottom = min(max(y_hi - ny + 2, 0), 2);
-    if (!left && !top && right + bottom == 0) return;  // uniform over the CTA
+    HaloSides h;
+    h.x_hi = min(bx0 + TX, nx);
+    h.y_hi = min(by0 + TY, ny);
+    h.left = bx0 == 0 ? 2 : 0;
+    h.top = by0 == 0 ? 2 : 0;
+    h.right = min(max(h.x_hi - nx + 2, 0), 2);
+    h.bottom = min(max(h.y_hi - ny + 2, 0), 2);
+    return h;
+}
+
+template <int NP, int TX, int TY, int NT>
+__device__ __forceinline__ void halo_load(HaloRegs<NP, TX, TY, NT> &hr, const HaloSides &hs,
+                                          const float *__restrict__ fin, int bx0, int by0, int nx, int ny,
+                                          int pitch, long long plane, int bc_x, int bc_y, int tid)
+{
+    using H = HaloRegs<NP, TX, TY, NT>;
     const long long base = (long long)GY * pitch + GX;
-    // x halo: rows by0 .. y_hi-1; item = (plane, row, ghost column j of 2)
+#pragma unroll
     for (int side = 0; side < 2; ++side) {
-        const int need = side == 0 ? (left ? 2 : 0) : right;
+        const int need = side == 0 ? hs.left : hs.right;
         if (need == 0) continue;
-        for (int it = tid; it < 2 * TY * NP; it += nthr) {
+#pragma unroll
+        for (int k = 0; k < H::XK; ++k) {
+            const int it = tid + k * NT;
             const int j = it & 1, r = (it >> 1) % TY, p = (it >> 1) / TY;
             const int y = by0 + r;
-            if (j >= need || y >= y_hi) continue;
-            const int xg = side == 0 ? j - 2 : nx + j;
-            const int xs = halo_source(xg, nx, bc_x);
-            tile[p * PS + (r + 2) * BX + (xg - bx0 + 4)] = fin[p * plane + base + (long long)y * pitch + xs];
+            if (it < H::XI && j < need && y < hs.y_hi) {
+                const int xs = halo_source(side == 0 ? j - 2 : nx + j, nx, bc_x);
+                hr.x[side][k] = fin[p * plane + base + (long long)y * pitch + xs];
+            }
         }
     }
-    // y halo: columns bx0 .. x_hi-1; item = (plane, ghost row j of 2, column)
+#pragma unroll
     for (int side = 0; side < 2; ++side) {
-        const int need = side == 0 ? (top ? 2 : 0) : bottom;
+        const int need = side == 0 ? hs.top : hs.bottom;
         if (need == 0) continue;
-        for (int it = tid; it < 2 * TX * NP; it += nthr) {
+#pragma unroll
+        for (int k = 0; k < H::YK; ++k) {
+            const int it = tid + k * NT;
             const int c = it % TX, j = (it / TX) & 1, p = it / (2 * TX);
             const int x = bx0 + c;
-            if (j >= need || x >= x_hi) continue;
+            if (it < H::YI && j < need && x < hs.x_hi) {
+                const int ys = halo_source(side == 0 ? j - 2 : ny + j, ny, bc_y);
+                hr.y[side][k] = fin[p * plane + base + (long long)ys * pitch + x];
+            }
+        }
+    }
+}
+
+// The halo of a boundary tile straight from the input into the tile, then
+// a barrier (the same items as halo_load / halo_store, without holding them
+// in registers: for kernels whose boundary tiles are rare, where the extra
+// registers would cost every tile).  All threads of the CTA call this for a
+// boundary tile.
+template <int NP, int TX, int TY, int NT>
+__device__ __forceinline__ void halo_fill(const HaloSides &hs, float *tile, const float *__restrict__ fin, int bx0,
+                                          int by0, int nx, int ny, int pitch, long long plane, int bc_x, int bc_y,
+                                          int tid)
+{
+    using H = HaloRegs<NP, TX, TY, NT>;
+    constexpr int BX = TX + 8, PS = (TY + 4) * BX;
+    const long long base = (long long)GY * pitch + GX;
+    for (int side = 0; side < 2; ++side) {
+        const int need = side == 0 ? hs.left : hs.right;
+        if (need == 0) continue;
+        for (int it = tid; it < H::XI; it += NT) {
+            const int j = it & 1, r = (it >> 1) % TY, p = (it >> 1) / TY;
+            const int y = by0 + r;
+            if (j >= need || y >= hs.y_hi) continue;
+            const int xg = side == 0 ? j - 2 : nx + j;
+            tile[p * PS + (r + 2) * BX + (xg - bx0 + 4)] =
+                fin[p * plane + base + (long long)y * pitch + halo_source(xg, nx, bc_x)];
+        }
+    }
+    for (int side = 0; side < 2; ++side) {
+        const int need = side == 0 ? hs.top : hs.bottom;
+        if (need == 0) continue;
+        for (int it = tid; it < H::YI; it += NT) {
+            const int c = it % TX, j = (it / TX) & 1, p = it / (2 * TX);
+            const int x = bx0 + c;
+            if (j >= need || x >= hs.x_hi) continue;
             const int yg = side == 0 ? j - 2 : ny + j;
-            const int ys = halo_source(yg, ny, bc_y);
-            tile[p * PS + (yg - by0 + 2) * BX + (c + 4)] = fin[p * plane + base + (long long)ys * pitch + x];
+            tile[p * PS + (yg - by0 + 2) * BX + (c + 4)] =
+                fin[p * plane + base + (long long)halo_source(yg, ny, bc_y) * pitch + x];
+        }
+    }
+    __syncthreads();
+}
+
+// Store the values halo_load fetched into the tile, then a barrier.  All
+// threads of the CTA call this for a boundary tile.
+template <int NP, int TX, int TY, int NT>
+__device__ __forceinline__ void halo_store(const HaloRegs<NP, TX, TY, NT> &hr, const HaloSides &hs, float *tile,
+                                           int bx0, int by0, int nx, int ny, int tid)
+{
+    using H = HaloRegs<NP, TX, TY, NT>;
+    constexpr int BX = TX + 8, PS = (TY + 4) * BX;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int need = side == 0 ? hs.left : hs.right;
+        if (need == 0) continue;
+#pragma unroll
+        for (int k = 0; k < H::XK; ++k) {
+            const int it = tid + k * NT;
+            const int j = it & 1, r = (it >> 1) % TY, p = (it >> 1) / TY;
+            if (it < H::XI && j < need && by0 + r < hs.y_hi) {
+                const int xg = side == 0 ? j - 2 : nx + j;
+                tile[p * PS + (r + 2) * BX + (xg - bx0 + 4)] = hr.x[side][k];
+            }
+        }
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int need = side == 0 ? hs.top : hs.bottom;
+        if (need == 0) continue;
+#pragma unroll
+        for (int k = 0; k < H::YK; ++k) {
+            const int it = tid + k * NT;
+            const int c = it % TX, j = (it / TX) & 1, p = it / (2 * TX);
+            if (it < H::YI && j < need && bx0 + c < hs.x_hi) {
+                const int yg = side == 0 ? j - 2 : ny + j;
+                tile[p * PS + (yg - by0 + 2) * BX + (c + 4)] = hr.y[side][k];
+            }
         }
     }
     __syncthreads();
@@ -983,6 +1121,8 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
     }
     __syncthreads();
     if (leader) tma_tile_load(tile, reinterpret_cast<unsigned long long>(&tmap), bx0, by0, b, BYTES);
+    const int tid = ty * (TX / CW) + tx;
+    const HaloSides hs = halo_sides<TX, TY>(bx0, by0, c.nx, c.ny);
     const bool ok = mbar_wait(b, 0, c.wait_polls);
     if (__syncthreads_or(!ok)) {
         // the copy did not land: report, give it one more bounded wait so
@@ -992,8 +1132,7 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
         mbar_wait(b, 0, TMA_WAIT_LIMIT);
         return;
     }
-    fill_tile_halo<NP, TX, TY>(tile, fin, bx0, by0, c.nx, c.ny, c.pitch, c.plane, c.bc_x, c.bc_y,
-                               ty * (TX / CW) + tx, NT);
+    if (hs.any()) halo_fill<NP, TX, TY, NT>(hs, tile, fin, bx0, by0, c.nx, c.ny, c.pitch, c.plane, c.bc_x, c.bc_y, tid);
     const int x = bx0 + CW * tx, y = by0 + ty;
     if (x >= c.nx || y >= c.ny) return;
     StateOutNoImages o{fout, c.plane};
