@@ -1,0 +1,10 @@
+// dbm_aux_s8.cu -- the output and initialisation launches for 8 species.
+#include "dbm_aux_impl.cuh"
+
+namespace dbm {
+template void aux_set_state<8>(dbm_handle *, void *, const double *, const double *, const double *, const double *,
+                                cudaStream_t);
+template void aux_moments<8>(dbm_handle *, const void *, double *, cudaStream_t);
+template void aux_noneq<8>(dbm_handle *, const void *, double *, cudaStream_t);
+template void aux_cons<8>(dbm_handle *, const void *, double *, double *, cudaStream_t);
+}  // namespace dbm

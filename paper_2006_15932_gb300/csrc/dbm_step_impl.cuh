@@ -230,13 +230,15 @@ __device__ __forceinline__ V resid4(const float k[4], V c0, V c1, V c2, V c3, V 
     return vfma(bc<V>(-k[3]), c3, vfma(bc<V>(-k[2]), c2, vfma(bc<V>(-k[1]), c1, vfma(bc<V>(-k[0]), c0, t))));
 }
 
-__device__ __forceinline__ float sr_round(double x, float u);
 __device__ __forceinline__ float sr_uniform(unsigned h, int k);
+__device__ __forceinline__ float ff_prod(float a, float b, float &e);
+__device__ __forceinline__ float ff_sum(float a, float b, float &e);
+__device__ __forceinline__ float sr_ff(float hi, float lo, float u);
 
 // Solve the symmetry blocks (out: ring means A[4], B[2], H[2], X[4], Y[4])
 // and project the result onto exact mass, energy and momentum.  With SR the
 // projected ring means, which carry the equilibrium's mass and energy, are
-// formed exactly (in double) and rounded stochastically (random numbers
+// formed exactly (float-float) and rounded stochastically (random numbers
 // kb..kb+3 of the cell hashes h): a round-to-nearest result misses the mass
 // target by a rounding error that follows the slowly varying macroscopic
 // state, and so adds up over the steps instead of averaging out.
@@ -268,9 +270,12 @@ __device__ __forceinline__ void solve_blocks(const K &k, int s, const V c[16], V
             using L = Lanes<V>;
 #pragma unroll
             for (int j = 0; j < L::n; ++j) {
-                const double x = fma((double)k.eqA[s][r][1], (double)L::get(de, j),
-                                     fma((double)k.eqA[s][r][0], (double)L::get(dm, j), (double)L::get(o[r], j)));
-                L::set(o[r], j, sr_round(x, sr_uniform(h[j], kb + r)));
+                // o + eqA0 dm + eqA1 de = s + (e3 + e4) + (e1 + e2) exactly
+                float e1, e2, e3, e4;
+                const float p1 = ff_prod(k.eqA[s][r][0], L::get(dm, j), e1);
+                const float p2 = ff_prod(k.eqA[s][r][1], L::get(de, j), e2);
+                const float s1 = ff_sum(ff_sum(L::get(o[r], j), p1, e3), p2, e4);
+                L::set(o[r], j, sr_ff(s1, __fadd_rn(__fadd_rn(e3, e4), __fadd_rn(e1, e2)), sr_uniform(h[j], kb + r)));
             }
         } else {
             o[r] = vfma(bc<V>(k.eqA[s][r][1]), de, vfma(bc<V>(k.eqA[s][r][0]), dm, o[r]));
@@ -315,6 +320,30 @@ __device__ __forceinline__ V nnd_diff_neg(V fm1, V f0, V fp1, V fp2)
     return vfma(bc<V>(-0.5f), vsub(vmm(d2, d3), vmm(d1, d2)), d2);
 }
 
+// The same x-direction flux differences for the pair of cells (x, x + 1),
+// from the two aligned 64-bit loads a = (f_{x-2}, f_{x-1}) and
+// b = (f_{x+2}, f_{x+3}) and the pair's own values c = (f_x, f_{x+1}): the
+// odd shifts are assembled from registers, and the limiter of the face
+// between the two cells is evaluated once (the second cell's left-face
+// minmod is the first cell's right-face minmod, with the same operands), so
+// the result is bitwise that of nnd_diff_pos / nnd_diff_neg.
+__device__ __forceinline__ float2 nnd_diff_pos_pair(float2 a, float2 c, float2 b)
+{
+    const float2 fm1 = make_float2(a.y, c.x), fp1 = make_float2(c.y, b.x);
+    const float2 d0 = vsub(fm1, a), d1 = vsub(c, fm1), d2 = vsub(fp1, c);
+    const float2 m12 = vmm(d1, d2);
+    const float2 m01 = make_float2(minmod(d0.x, d1.x), m12.x);
+    return vfma(bc<float2>(0.5f), vsub(m12, m01), d1);
+}
+__device__ __forceinline__ float2 nnd_diff_neg_pair(float2 a, float2 c, float2 b)
+{
+    const float2 fm1 = make_float2(a.y, c.x), fp1 = make_float2(c.y, b.x);
+    const float2 d1 = vsub(c, fm1), d2 = vsub(fp1, c), d3 = vsub(b, fp1);
+    const float2 m23 = vmm(d2, d3);
+    const float2 m12 = make_float2(minmod(d1.x, d2.x), m23.x);
+    return vfma(bc<float2>(-0.5f), vsub(m23, m12), d2);
+}
+
 // Ghost-image bitmask of interior index k on an axis of n cells: bit j set
 // when ghost index {-2, -1, n, n+1}[j] takes its value from cell k.
 __device__ __forceinline__ unsigned ghost_mask(int k, int n, int bc)
@@ -354,7 +383,7 @@ __device__ __forceinline__ void store_images(T *pl, int x, int y, int nx, int ny
 // W - p = s + se exactly (Knuth's two-sum), so the numerator is as accurate
 // as an FP64 evaluation while every operation stays on the FP32 pipes.  The
 // _rn intrinsics keep the compiler from contracting these steps.
-__device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux, float uy)
+__device__ __forceinline__ void mixture_T_num(float W, float w, float ux, float uy, float &hi, float &lo)
 {
     const float u2 = __fmaf_rn(ux, ux, __fmul_rn(uy, uy));
     const float p = __fmul_rn(u2, w);
@@ -362,7 +391,14 @@ __device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux,
     const float s = __fsub_rn(W, p);
     const float bb = __fsub_rn(s, W);
     const float se = __fadd_rn(__fsub_rn(W, __fsub_rn(s, bb)), __fsub_rn(-p, bb));
-    return __fadd_rn(s, __fsub_rn(se, pe)) / wd;
+    hi = s;
+    lo = __fsub_rn(se, pe);
+}
+__device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux, float uy)
+{
+    float hi, lo;
+    mixture_T_num(W, w, ux, uy, hi, lo);
+    return __fadd_rn(hi, lo) / wd;
 }
 
 // Stochastic rounding (dbm_params.rounding = DBM_ROUND_STOCHASTIC).  The
@@ -391,6 +427,36 @@ __device__ __forceinline__ float sr_round(double x, float u)
 {
     const float s = __double2float_rn(x);
     return sr_finish(s, __double2float_rn(x - (double)s), u);
+}
+// Error-free transformations on the FP32 pipes: a b = p + e (FMA residual)
+// and a + b = s + e (Knuth's two-sum), exactly.
+__device__ __forceinline__ float ff_prod(float a, float b, float &e)
+{
+    const float p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+    return p;
+}
+__device__ __forceinline__ float ff_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+// hi + lo rounded stochastically; renormalised first, so that the head is
+// the round-to-nearest value and the tail its rounding error.
+__device__ __forceinline__ float sr_ff(float hi, float lo, float u)
+{
+    float e;
+    const float s = ff_sum(hi, lo, e);
+    return sr_finish(s, e, u);
+}
+// c + a b rounded stochastically.
+__device__ __forceinline__ float sr_fma(float a, float b, float c, float u)
+{
+    float pe, se;
+    const float s = ff_sum(c, ff_prod(a, b, pe), se);
+    return sr_ff(s, __fadd_rn(se, pe), u);
 }
 // The k-th uniform number in [0, 1) of a cell whose hash is h: a Weyl
 // sequence (golden-ratio increments) from h, top 24 bits.
@@ -621,20 +687,21 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
             }
         }
         // stochastic rounding: the mixture T, from which every species'
-        // equilibrium energy follows, rounded without bias (the float-float
-        // numerator, or the double T, evaluated in double)
+        // equilibrium energy follows, rounded without bias (the double T, or
+        // the quotient of the float-float numerator with its remainder)
         if (sr) {
 #pragma unroll
             for (int j = 0; j < L::n; ++j) {
-                double Td;
                 if (t64) {
-                    Td = T64[j];
+                    L::set(T, j, sr_round(T64[j], sr_uniform(hcell[j], 0)));
                 } else {
-                    const double u0 = L::get(ux, j), u1 = L::get(uy, j);
-                    Td = ((double)L::get(we, j) - fma(u0, u0, u1 * u1) * (double)L::get(w, j)) / (double)L::get(wd, j);
+                    float nh, nl;
+                    mixture_T_num(L::get(we, j), L::get(w, j), L::get(ux, j), L::get(uy, j), nh, nl);
+                    const float wdj = L::get(wd, j);
+                    const float q = __fadd_rn(nh, nl) / wdj;
+                    const float r = __fadd_rn(__fmaf_rn(-q, wdj, nh), nl);  // (nh + nl) - q wd
+                    L::set(T, j, sr_ff(q, r / wdj, sr_uniform(hcell[j], 0)));
                 }
-                T64[j] = Td;
-                L::set(T, j, sr_round(Td, sr_uniform(hcell[j], 0)));
             }
         }
     }
@@ -724,24 +791,21 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
                     if (t64 || sr) {
 #pragma unroll
                         for (int j = 0; j < L::n; ++j) {
-                            double nd, Td;
+                            const float un = sr_uniform(hcell[j], S * Q + 1 + s);
+                            const float uT = sr_uniform(hcell[j], S * Q + 1 + S + s);
                             if (t64) {
                                 double n_s = 0.0;
 #pragma unroll
                                 for (int q = 0; q < S; ++q)
                                     if (q == s) n_s = n64[q][j];
-                                nd = fma(xa.tau_a[s], om64[j], n_s);
-                                Td = fma(xa.tau_d[s], dT64[j], T64[j]);
-                            } else {  // n + tau a omega exactly (the product of two floats is exact in double)
-                                nd = fma((double)g.tau_a[s], (double)L::get(om, j), (double)L::get(ns, j));
-                                Td = fma((double)g.tau_d[s], (double)L::get(dT, j), (double)L::get(T, j));
+                                const double nd = fma(xa.tau_a[s], om64[j], n_s);
+                                const double Td = fma(xa.tau_d[s], dT64[j], T64[j]);
+                                L::set(nr, j, sr ? sr_round(nd, un) : __double2float_rn(nd));
+                                L::set(Ts, j, sr ? sr_round(Td, uT) : __double2float_rn(Td));
+                            } else {  // n + tau a omega and T + tau T' exactly, then rounded
+                                L::set(nr, j, sr_fma(g.tau_a[s], L::get(om, j), L::get(ns, j), un));
+                                L::set(Ts, j, sr_fma(g.tau_d[s], L::get(dT, j), L::get(T, j), uT));
                             }
-                            L::set(nr, j, sr ? sr_round(nd, sr_uniform(hcell[j], S * Q + 1 + s))
-                                             : __double2float_rn(nd));
-                            if (sr)
-                                L::set(Ts, j, sr_round(Td, sr_uniform(hcell[j], S * Q + 1 + S + s)));
-                            else if (t64)
-                                L::set(Ts, j, __double2float_rn(Td));
                         }
                     }
                 }
@@ -751,13 +815,21 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
             }
             fhat_blocks<V>(nr, ux, uy, vmul(Ts, bc<V>(c.inv_m[s])), c.dpi[s], cb);
             if constexpr (X::on) {
-                if (sr) {  // the energy target n* ((D+I) T*/m + u.u) formed in double, rounded without bias
+                if (sr) {  // the energy target n* ((D+I) T*/m + u.u) formed in float-float, rounded without bias
 #pragma unroll
                     for (int j = 0; j < L::n; ++j) {
-                        const double u0 = L::get(ux, j), u1 = L::get(uy, j);
-                        const double th = (double)L::get(Ts, j) * (double)c.inv_m[s];
-                        const double e1 = (double)L::get(nr, j) * fma((double)c.dpi[s], th, fma(u0, u0, u1 * u1));
-                        L::set(cb[1], j, sr_round(e1, sr_uniform(hcell[j], S * Q + 1 + 6 * S + s)));
+                        float thl, al, xl, yl, e1, e2, cl;
+                        const float th = ff_prod(L::get(Ts, j), c.inv_m[s], thl);  // T*/m
+                        const float a1 = ff_prod(c.dpi[s], th, al);
+                        const float x2 = ff_prod(L::get(ux, j), L::get(ux, j), xl);
+                        const float y2 = ff_prod(L::get(uy, j), L::get(uy, j), yl);
+                        const float u2 = ff_sum(x2, y2, e1);
+                        const float r1 = ff_sum(a1, u2, e2);  // (D+I) T*/m + u.u = r1 + r1l
+                        const float r1l = __fadd_rn(__fadd_rn(e2, __fmaf_rn(c.dpi[s], thl, al)),
+                                                    __fadd_rn(e1, __fadd_rn(xl, yl)));
+                        const float nrj = L::get(nr, j);
+                        const float c1 = ff_prod(nrj, r1, cl);
+                        L::set(cb[1], j, sr_ff(c1, __fmaf_rn(nrj, r1l, cl), sr_uniform(hcell[j], S * Q + 1 + 6 * S + s)));
                     }
                 }
             }
@@ -840,12 +912,21 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
                 }
             }
             V f1 = vfma(dtt, vsub(e, f0[i]), f0[i]);
-            if (dir_x(i) > 0)
+            if constexpr (L::n == 2) {
+                if (dir_x(i) != 0) {
+                    const V a = t.ld(p, -2, 0), b = t.ld(p, 2, 0);
+                    if (dir_x(i) > 0)
+                        f1 = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos_pair(a, f0[i], b), f1);
+                    else
+                        f1 = vfma(bc<V>(c.cdx[s][r]), nnd_diff_neg_pair(a, f0[i], b), f1);
+                }
+            } else if (dir_x(i) > 0) {
                 f1 = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos<V>(t.ld(p, -2, 0), t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0)),
                           f1);
-            else if (dir_x(i) < 0)
+            } else if (dir_x(i) < 0) {
                 f1 = vfma(bc<V>(c.cdx[s][r]), nnd_diff_neg<V>(t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0), t.ld(p, 2, 0)),
                           f1);
+            }
             if (dir_y(i) > 0)
                 f1 = vfma(bc<V>(-c.cdy[s][r]), nnd_diff_pos<V>(t.ld(p, 0, -2), t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1)),
                           f1);

@@ -19,7 +19,10 @@ Requests (``workloads.RequestSpec``) arrive over time.  The server
   ones join, and the batch is rebuilt for the new membership;
 * finishes a request by reading its conserved totals (and optionally its
   final state) into pinned host memory; the request's latency runs from its
-  arrival to the moment that copy has completed.
+  arrival to the moment that copy has completed;
+* withdraws a request at its ``cancel_at`` time: a waiting one at once, a
+  running one at its group's next quantum boundary, when none of its work
+  is in flight, releasing its memory.
 
 ``run_sequential`` is the baseline: the same requests solved first come,
 first served, one at a time, in FP64 or FP32.
@@ -97,6 +100,7 @@ class Result:
     status: int
     conservation: np.ndarray
     f: Optional[np.ndarray] = None
+    cancelled: bool = False  # withdrawn before it finished (no result state)
 
     @property
     def latency(self) -> float:
@@ -114,6 +118,7 @@ class _Active:
     nbytes: int
     admitted: float
     remaining: int
+    cancelled: bool = False
 
 
 @dataclass
@@ -191,14 +196,17 @@ class Server:
             ev.record(g.stream)
         return _Done(active=a, stream=g.stream, event=ev, cons=host, f=fh)
 
-    def _advance(self, g: _Group, done: List[_Done]) -> None:
-        """Between quanta: retire finished members, take in new ones, launch
-        the next quantum."""
+    def _advance(self, g: _Group, done: List[_Done], dropped: List[_Active]) -> None:
+        """Between quanta (no work of the group in flight): retire finished
+        and cancelled members, take in new ones, launch the next quantum."""
         torch = self.torch
         changed = bool(g.incoming)
         keep = []
         for a in g.members + g.incoming:
-            if a.remaining == 0:
+            if a.cancelled:
+                dropped.append(a)
+                changed = True
+            elif a.remaining == 0:
                 done.append(self._finish(g, a))
                 changed = True
             else:
@@ -245,9 +253,26 @@ class Server:
         done: List[_Done] = []
         results: List[Result] = []
         t0 = time.perf_counter()
+
+        def withdrawn(spec, admitted, now):
+            return Result(rid=spec.rid, ns=spec.ns, cells=spec.cells, nsteps=spec.nsteps, arrival=spec.arrival,
+                          admitted=admitted, finished=now, status=0, conservation=np.zeros(0), cancelled=True)
+
         while pending or queue or done or any(g.members or g.incoming or g.busy for g in self.groups.values()):
             now = time.perf_counter() - t0
             progressed = False
+            # cancellations: waiting requests leave at once, running ones at
+            # their group's next quantum boundary (their memory is released then)
+            due = lambda q: q.cancel_at is not None and q.cancel_at <= now
+            for wait in (pending, queue):
+                for spec in [q for q in wait if due(q)]:
+                    wait.remove(spec)
+                    results.append(withdrawn(spec, None, now))
+                    progressed = True
+            for g in self.groups.values():
+                for a in g.members + g.incoming:
+                    if due(a.spec):
+                        a.cancelled = True
             while pending and pending[0].arrival <= now:
                 queue.append(pending.popleft())
             while queue and self.adm.fits(sizes[queue[0].rid]):
@@ -259,7 +284,12 @@ class Server:
                 if g.busy and g.event.query():
                     g.busy = False
                 if not g.busy and (g.members or g.incoming):
-                    self._advance(g, done)
+                    dropped: List[_Active] = []
+                    self._advance(g, done, dropped)
+                    for a in dropped:
+                        a.solver.close()
+                        self.adm.release(a.nbytes)
+                        results.append(withdrawn(a.spec, a.admitted, time.perf_counter() - t0))
                     progressed = True
             still = []
             for d in done:
@@ -322,7 +352,9 @@ def run_sequential(specs: List[W.RequestSpec], precision: str = "fp64", device="
 
 def summarize(results: List[Result]) -> dict:
     """Latency percentiles and throughput (species-cell updates per second
-    from the first arrival to the last completion)."""
+    from the first arrival to the last completion) of the completed
+    requests."""
+    results = [r for r in results if not r.cancelled]
     lat = np.array([r.latency for r in results])
     t_first = min(r.arrival for r in results)
     t_last = max(r.finished for r in results)

@@ -18,7 +18,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field, replace
-from typing import List, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -293,7 +293,8 @@ def batched_instances(n: int = 64, seed: int = SEED, lo: int = 64, hi: int = 512
 class RequestSpec:
     """One serving request: an L x L instance of ``ns`` species, a shock
     tube or a reactive gas, advanced by ``nsteps`` steps; ``arrival`` in
-    seconds after the start of the run."""
+    seconds after the start of the run; ``cancel_at`` (seconds after the
+    start, or None) withdraws the request at that time."""
     rid: int
     kind: str
     L: int
@@ -301,6 +302,7 @@ class RequestSpec:
     seed: int
     nsteps: int
     arrival: float = 0.0
+    cancel_at: Optional[float] = None
 
     @property
     def units(self) -> int:  # species-cell updates the request asks for

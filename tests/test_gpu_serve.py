@@ -135,3 +135,26 @@ def test_sequential_fp64_baseline_matches_the_oracle(S, orc):
     for spec in specs:
         assert res[spec.rid].status == 0
         assert _rel(res[spec.rid].f, _oracle_final(orc, spec)) <= 1e-12
+
+
+def test_cancelled_requests_leave_and_the_others_are_unchanged(S):
+    """A request withdrawn while it waits leaves at once; one withdrawn while
+    it runs leaves its group at the next quantum boundary; their memory is
+    returned, and every other request's result is bitwise its result alone."""
+    import dataclasses
+
+    specs = _mix()
+    specs[8] = dataclasses.replace(specs[8], arrival=5.0, cancel_at=0.001)  # still waiting when withdrawn
+    specs[2] = dataclasses.replace(specs[2], nsteps=10 ** 6, cancel_at=0.05)  # running when withdrawn
+    srv = S.Server(qmax=8, keep_f=True, hbm_budget=1 << 32)
+    res = {r.rid: r for r in srv.run(specs)}
+    assert sorted(res) == [s.rid for s in specs]
+    assert res[8].cancelled and res[8].admitted is None
+    assert res[2].cancelled and res[2].admitted is not None
+    assert srv.adm.used == 0
+    for spec in specs:
+        if spec.rid in (2, 8):
+            continue
+        r = res[spec.rid]
+        assert not r.cancelled and r.status == 0
+        np.testing.assert_array_equal(_alone(S, spec).f, r.f)

@@ -96,3 +96,13 @@ def test_request_fields_and_problem(kind, ns):
         rho = rho_s.sum(0)
         assert set(torch.unique(rho).tolist()) == {0.125, 1.0}
         assert torch.allclose(rho * T, torch.where(rho > 0.5, 1.0, 0.1).to(torch.float64))
+
+
+def test_summary_leaves_out_withdrawn_requests():
+    mk = lambda rid, fin, cancelled=False: serve.Result(rid=rid, ns=2, cells=100, nsteps=10, arrival=0.0,
+                                                        admitted=0.0, finished=fin, status=0,
+                                                        conservation=np.zeros(6), cancelled=cancelled)
+    rs = [mk(0, 1.0), mk(1, 3.0), mk(2, 0.1, cancelled=True)]
+    d = serve.summarize(rs)
+    assert d["requests"] == 2 and d["units"] == 2 * 2000
+    assert d["makespan_s"] == 3.0 and d["p50_s"] == 2.0
