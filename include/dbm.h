@@ -25,7 +25,15 @@
  *    a scalar field is [ny][nx], a species field [S][ny][nx], a distribution
  *    [S][16][ny][nx].  They may live in device memory or in page-locked host
  *    memory that the device can address (cudaHostAlloc / cudaHostRegister);
- *    pageable host memory is not accepted.
+ *    pageable host memory is accepted only where the device can read it in
+ *    place (cudaDevAttrPageableMemoryAccess), else refused with
+ *    DBM_ERR_INVALID.  dbm_set_state and dbm_moments move page-locked host
+ *    fields through the handle's second state buffer (free between steps;
+ *    the next step overwrites it) with one stream-ordered copy each, so the
+ *    copy engine carries them and no SM waits on the host link; where that
+ *    buffer is too small (one species, or BF16DEV moments) the kernels read
+ *    or write the host memory directly.  Either way the results are the
+ *    same bits as with device arrays.
  *  - Velocity index i = 0..15 runs over the rings a, b, c, d (4 each) in the
  *    order of the D2V16 definition: axis rings (v,0), (0,v), (-v,0), (0,-v);
  *    diagonal rings (v,v), (-v,v), (-v,-v), (v,-v).
@@ -95,7 +103,8 @@ enum dbm_status_code {
     DBM_ERR_NONFINITE = -5,   /* device health flag: a non-finite moment        */
     DBM_ERR_NEGATIVE = -6,    /* device health flag: negative density, T <= 0 or n* < 0 */
     DBM_ERR_STABILITY = -7,   /* CFL or dt/tau stability limit exceeded         */
-    DBM_ERR_TIMEOUT = -8      /* device health flag: a bounded wait gave up     */
+    DBM_ERR_TIMEOUT = -8,     /* device health flag: a bounded wait gave up     */
+    DBM_ERR_BOUNDS = -9       /* device health flag (checked builds): an index out of range */
 };
 
 /* Health-flag bits as kept on the device (dbm_status_bits). */
@@ -104,7 +113,10 @@ enum dbm_health_bits {
     DBM_HEALTH_TEMPERATURE = 2,  /* mixture T <= 0 or not finite */
     DBM_HEALTH_NSTAR = 4,        /* n^s* < 0 after the reaction  */
     DBM_HEALTH_NONFINITE = 8,    /* a non-finite moment           */
-    DBM_HEALTH_TIMEOUT = 16      /* a tile copy did not complete within its wait limit */
+    DBM_HEALTH_TIMEOUT = 16,     /* a tile copy did not complete within its wait limit */
+    DBM_HEALTH_BOUNDS = 32       /* checked builds only (-DDBM_CHECKED): an index fell
+                                    outside the buffer it addresses; the access was
+                                    skipped */
 };
 
 /* Step kernel selection (dbm_params.step_kernel).  Every choice runs the

@@ -486,6 +486,36 @@ static int check_bound(dbm_handle *h)
     return DBM_OK;
 }
 
+// Where a field array lives: device memory (or host memory the device reads
+// in place), page-locked host memory, or pageable host memory the device
+// cannot reach (refused rather than passed to a kernel).
+enum { MEM_DEVICE = 0, MEM_PINNED = 1, MEM_UNREACHABLE = 2 };
+
+static int mem_kind(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return MEM_UNREACHABLE;
+    }
+    if (a.type == cudaMemoryTypeHost) return MEM_PINNED;
+    if (a.type == cudaMemoryTypeUnregistered) {
+        int dev = 0, pageable = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev);
+        return pageable ? MEM_DEVICE : MEM_UNREACHABLE;
+    }
+    return MEM_DEVICE;
+}
+
+// Staging area for transfers between page-locked host memory and a call:
+// the state buffer the next step will overwrite (free between steps), when
+// it holds `bytes`; NULL otherwise.
+static char *staging(dbm_handle *h, size_t bytes)
+{
+    return h->lay.bytes >= bytes ? (char *)h->f[h->cur ^ 1] : nullptr;
+}
+
 int dbm_set_state(dbm_handle *h, const double *rho_s, const double *ux, const double *uy,
                   const double *T, void *stream)
 {
@@ -493,9 +523,36 @@ int dbm_set_state(dbm_handle *h, const double *rho_s, const double *ux, const do
     if (rc) return rc;
     if (!rho_s || !ux || !uy || !T) return fail(h, DBM_ERR_INVALID, "set_state: null field");
     cudaStream_t st = (cudaStream_t)stream;
+    // fields in page-locked host memory are copied (copy engine, no SM time)
+    // into the free state buffer and read from there, when they fit
+    const size_t N = (size_t)h->p.nx * h->p.ny, S = h->p.nspecies;
+    const double *src[4] = {rho_s, ux, uy, T};
+    const size_t len[4] = {S * N, N, N, N};
+    int kind[4];
+    bool any_pinned = false;
+    for (int k = 0; k < 4; ++k) {
+        kind[k] = mem_kind(src[k]);
+        if (kind[k] == MEM_UNREACHABLE)
+            return fail(h, DBM_ERR_INVALID, "set_state: field %d is in pageable host memory the device cannot read", k);
+        any_pinned |= kind[k] == MEM_PINNED;
+    }
+    char *stg = any_pinned ? staging(h, (S + 3) * N * sizeof(double)) : nullptr;
+    if (stg) {
+        size_t off = 0;
+        for (int k = 0; k < 4; ++k) {
+            if (kind[k] == MEM_PINNED) {
+                rc = set_cuda_error(h, cudaMemcpyAsync(stg + off, src[k], len[k] * sizeof(double),
+                                                       cudaMemcpyHostToDevice, st),
+                                    "set_state: copy of a host field");
+                if (rc) return rc;
+                src[k] = (const double *)(stg + off);
+            }
+            off += len[k] * sizeof(double);
+        }
+    }
     rc = set_cuda_error(h, cudaMemsetAsync(h->scratch, 0, SCRATCH_HEAD, st), "clear health flag");
     if (rc) return rc;
-    rc = launch_set_state(h, h->f[h->cur], rho_s, ux, uy, T, st);
+    rc = launch_set_state(h, h->f[h->cur], src[0], src[1], src[2], src[3], st);
     if (rc == DBM_OK) h->steps = 0;
     return rc;
 }
@@ -543,7 +600,18 @@ int dbm_moments(dbm_handle *h, double *out, void *stream)
     int rc = check_bound(h);
     if (rc) return rc;
     if (!out) return fail(h, DBM_ERR_INVALID, "moments: null out");
-    return launch_moments(h, h->f[h->cur], out, (cudaStream_t)stream);
+    const int kind = mem_kind(out);
+    if (kind == MEM_UNREACHABLE)
+        return fail(h, DBM_ERR_INVALID, "moments: out is in pageable host memory the device cannot write");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)(4 * h->p.nspecies + 5) * h->p.nx * h->p.ny * sizeof(double);
+    char *stg = kind == MEM_PINNED ? staging(h, bytes) : nullptr;
+    if (!stg) return launch_moments(h, h->f[h->cur], out, st);
+    // page-locked host output: the fields go to the free state buffer, then
+    // one copy (copy engine, no SM time) to the host
+    rc = launch_moments(h, h->f[h->cur], (double *)stg, st);
+    if (rc) return rc;
+    return set_cuda_error(h, cudaMemcpyAsync(out, stg, bytes, cudaMemcpyDeviceToHost, st), "moments: copy to host");
 }
 
 int dbm_nonequilibrium(dbm_handle *h, double *out, void *stream)
@@ -591,6 +659,7 @@ int dbm_status(dbm_handle *h, void *stream, unsigned *bits)
     rc = set_cuda_error(h, cudaStreamSynchronize(st), "synchronise for health flag");
     if (rc) return rc;
     if (bits) *bits = v;
+    if (v & DBM_HEALTH_BOUNDS) return fail(h, DBM_ERR_BOUNDS, "an index fell outside its buffer (flag %u)", v);
     if (v & DBM_HEALTH_TIMEOUT) return fail(h, DBM_ERR_TIMEOUT, "a tile copy timed out (flag %u)", v);
     if (v & DBM_HEALTH_NONFINITE) return fail(h, DBM_ERR_NONFINITE, "non-finite moment (flag %u)", v);
     if (v) return fail(h, DBM_ERR_NEGATIVE, "non-positive density/temperature or negative n* (flag %u)", v);

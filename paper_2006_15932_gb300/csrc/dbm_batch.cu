@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
         const int tid = ty * (TX / CW) + tx;
         const HaloSides hs = halo_sides<TX, TY>(cur.bx0, cur.by0, g.nx, g.ny);
         HaloRegs<NP, TX, TY, NT> hr;
-        if (hs.any()) halo_load(hr, hs, e.fin, cur.bx0, cur.by0, g.nx, g.ny, g.pitch, g.plane, g.bc_x, g.bc_y, tid);
+        if (hs.any())
+            halo_load(hr, hs, e.fin, cur.bx0, cur.by0, g.nx, g.ny, g.pitch, g.plane, g.bc_x, g.bc_y, tid, e.flag);
         const bool ok = mbar_wait(b, phase, g.wait_polls);
         if (__syncthreads_or(!ok)) {
             // the copy did not land: report, give it one more bounded wait so
@@ -172,16 +173,16 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
             mbar_wait(b, phase, TMA_WAIT_LIMIT);
             return;
         }
-        if (hs.any()) halo_store(hr, hs, tile, cur.bx0, cur.by0, g.nx, g.ny, tid);
+        if (hs.any()) halo_store(hr, hs, tile, cur.bx0, cur.by0, g.nx, g.ny, tid, e.flag);
         const int x = cur.bx0 + CW * tx, y = cur.by0 + ty;
         if (x < g.nx && y < g.ny) {
-            StateOutNoImages o{e.fout, g.plane};
+            StateOutNoImages o{e.fout, g.plane, (long long)NP * g.plane, e.flag};
             const float *base = tile + (ty + 2) * BX + (CW * tx + 4);
             if constexpr (CW == 2) {
-                const SmemTile2 st{base, BY * BX, BX};
+                const SmemTile2 st{base, BY * BX, BX, tile, NP * BY * BX, e.flag};
                 step_cell<S>(P.hot, g, st, x, y, x + 1 < g.nx, o, e.flag);
             } else {
-                const SmemTile st{base, BY * BX, BX};
+                const SmemTile st{base, BY * BX, BX, tile, NP * BY * BX, e.flag};
                 step_cell<S>(P.hot, g, st, x, y, true, o, e.flag);
             }
         }

@@ -51,12 +51,13 @@ __global__ void __launch_bounds__(TX / CW * TY, bf16_ctas_per_sm(S, TX, TY))
                        : c.bc_y == DBM_BC_PERIODIC ? ((y % c.ny) + c.ny) % c.ny : min(max(y, 0), c.ny - 1);
         const long long cell = (long long)(ys + GY) * c.pitch + (xs + GX);
         float *dst = tile + rr * BX + cc;
+        const bool src_ok = ok && in_bounds(cell, in.P, flag);
 #pragma unroll 1
         for (int s = 0; s < S; ++s) {
             float f[Q];
-            if (ok) bf_cell_f<S>(c, in, s, cell, f);
+            if (src_ok) bf_cell_f<S>(c, in, s, cell, f);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) dst[(s * Q + i) * (BY * BX)] = ok ? f[i] : 0.0f;
+            for (int i = 0; i < Q; ++i) dst[(s * Q + i) * (BY * BX)] = src_ok ? f[i] : 0.0f;
         }
     }
     __syncthreads();
@@ -65,12 +66,12 @@ __global__ void __launch_bounds__(TX / CW * TY, bf16_ctas_per_sm(S, TX, TY))
     const int x = bx0 + CW * tx, y = by0 + ty;
     if (x >= c.nx || y >= c.ny) return;
     const float *base = tile + (ty + 2) * BX + (CW * tx + 2);
-    BfOut o{out, S};
+    BfOut o{out, S, flag};
     if constexpr (CW == 2) {
-        const SmemTile2 t{base, BY * BX, BX};
+        const SmemTile2 t{base, BY * BX, BX, tile, S * Q * BY * BX, flag};
         step_cell<S>(c, c, t, x, y, x + 1 < c.nx, o, flag);
     } else {
-        const SmemTile t{base, BY * BX, BX};
+        const SmemTile t{base, BY * BX, BX, tile, S * Q * BY * BX, flag};
         step_cell<S>(c, c, t, x, y, true, o, flag);
     }
 }

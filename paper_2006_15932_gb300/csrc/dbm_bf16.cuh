@@ -46,13 +46,17 @@ struct BfOut {
     static constexpr bool kNoImages = true;
     BfState st;
     int S;
+    unsigned *flag;  // checked builds: where an out-of-range index is reported
     __device__ __forceinline__ void put(const Site &w, int p, float g, float e) const
     {
-        __stcs(st.d + (long long)p * st.P + w.cell, __float2bfloat16_rn(g - e));
+        const long long i = (long long)p * st.P + w.cell;
+        if (in_bounds(i, 16LL * S * st.P, flag)) __stcs(st.d + i, __float2bfloat16_rn(g - e));
     }
     __device__ __forceinline__ void put(const Site &w, int p, float2 g, float2 e) const
     {
-        __nv_bfloat16 *q = st.d + (long long)p * st.P + w.cell;
+        const long long i = (long long)p * st.P + w.cell;
+        if (!in_bounds(i, 16LL * S * st.P - (w.two ? 1 : 0), flag)) return;
+        __nv_bfloat16 *q = st.d + i;
         if (w.two)
             __stcs(reinterpret_cast<__nv_bfloat162 *>(q), __floats2bfloat162_rn(g.x - e.x, g.y - e.y));
         else
@@ -60,11 +64,14 @@ struct BfOut {
     }
     __device__ __forceinline__ void put_f(const Site &w, long long plane, float v) const
     {
-        __stcs(st.mom + plane * st.P + w.cell, v);
+        const long long i = plane * st.P + w.cell;
+        if (in_bounds(i, (long long)(S + 3) * st.P, flag)) __stcs(st.mom + i, v);
     }
     __device__ __forceinline__ void put_f(const Site &w, long long plane, float2 v) const
     {
-        float *q = st.mom + plane * st.P + w.cell;
+        const long long i = plane * st.P + w.cell;
+        if (!in_bounds(i, (long long)(S + 3) * st.P - (w.two ? 1 : 0), flag)) return;
+        float *q = st.mom + i;
         if (w.two)
             __stcs(reinterpret_cast<float2 *>(q), v);
         else

@@ -101,4 +101,20 @@ __device__ __forceinline__ void raise_flag(unsigned *flag, unsigned bits)
     if (bits) atomicOr(flag, bits);
 }
 
+// Checked builds (-DDBM_CHECKED, a debugging aid that stands in for a
+// memory checker): every index into a shared-memory tile, a state buffer or
+// a ghost image is compared with the extent of what it addresses; one
+// outside it raises DBM_HEALTH_BOUNDS and the access is skipped (a load
+// gives 0).  The default build compiles the checks away.
+__device__ __forceinline__ bool in_bounds(long long i, long long n, unsigned *flag)
+{
+#ifdef DBM_CHECKED
+    if (i >= 0 && i < n) return true;
+    raise_flag(flag, DBM_HEALTH_BOUNDS);
+    return false;
+#else
+    return true;
+#endif
+}
+
 }  // namespace dbm

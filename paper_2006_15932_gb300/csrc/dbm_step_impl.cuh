@@ -150,7 +150,15 @@ struct GlobalTile {
     const float *base;  // plane 0, row y + GY, column x + GX
     long long P;        // plane stride
     long long py;       // row stride
-    __device__ __forceinline__ float ld(int p, int dx, int dy) const { return __ldg(base + p * P + dy * py + dx); }
+    const float *lo;    // checked builds: the buffer and its extent
+    long long n;
+    unsigned *flag;
+    __device__ __forceinline__ float ld(int p, int dx, int dy) const
+    {
+        const float *q = base + p * P + dy * py + dx;
+        if (!in_bounds(q - lo, n, flag)) return 0.0f;
+        return __ldg(q);
+    }
 };
 
 // Stencil values of one cell from a shared-memory tile [plane][row][column].
@@ -158,7 +166,15 @@ struct SmemTile {
     using V = float;
     const float *base;  // plane 0, this thread's row and column
     int P, py;
-    __device__ __forceinline__ float ld(int p, int dx, int dy) const { return base[p * P + dy * py + dx]; }
+    const float *lo;  // checked builds: the tile and its extent (floats)
+    int n;
+    unsigned *flag;
+    __device__ __forceinline__ float ld(int p, int dx, int dy) const
+    {
+        const float *q = base + p * P + dy * py + dx;
+        if (!in_bounds(q - lo, n, flag)) return 0.0f;
+        return *q;
+    }
 };
 
 // Stencil values of the cells (x, y) and (x + 1, y) from a shared-memory
@@ -168,9 +184,13 @@ struct SmemTile2 {
     using V = float2;
     const float *base;  // plane 0, this thread's row, its first column
     int P, py;
+    const float *lo;  // checked builds: the tile and its extent (floats)
+    int n;
+    unsigned *flag;
     __device__ __forceinline__ float2 ld(int p, int dx, int dy) const
     {
         const float *q = base + p * P + dy * py + dx;
+        if (!in_bounds(q - lo, n - 1, flag)) return make_float2(0.0f, 0.0f);
         if (dx & 1) return make_float2(q[0], q[1]);
         return *reinterpret_cast<const float2 *>(q);
     }
@@ -528,9 +548,12 @@ struct StateOut {
     float *f;  // plane 0 of the output buffer
     long long P;
     int nx, ny, pitch;
+    long long n;  // checked builds: elements of the buffer
+    unsigned *flag;
     __device__ __forceinline__ void put(const Site &w, int p, float g, float) const
     {
-        __stcs(f + (long long)p * P + w.cell, g);  // streamed: not re-read this step
+        const long long i = (long long)p * P + w.cell;
+        if (in_bounds(i, n, flag)) __stcs(f + i, g);  // streamed: not re-read this step
     }
     __device__ __forceinline__ void put_n(const Site &, int, float) const {}
     __device__ __forceinline__ void put_mix(const Site &, float, float, float) const {}
@@ -538,7 +561,9 @@ struct StateOut {
     {
         for (int i = 0; i < Q; ++i) {
             float *pl = f + (long long)(s * Q + i) * P;
-            store_images(pl, w.x, w.y, nx, ny, pitch, w.mx, w.my, pl[w.cell]);
+            // ghost images lie within rows -2 .. ny+1 and columns -2 .. nx+1
+            if (in_bounds((long long)(s * Q + i) * P + (long long)(ny + 1 + GY) * pitch + (nx + 1 + GX), n, flag))
+                store_images(pl, w.x, w.y, nx, ny, pitch, w.mx, w.my, pl[w.cell]);
         }
     }
     __device__ __forceinline__ void images_mix(const Site &) const {}
@@ -552,13 +577,18 @@ struct StateOutNoImages {
     static constexpr bool kNoImages = true;
     float *f;  // plane 0 of the output buffer
     long long P;
+    long long n;  // checked builds: elements of the buffer
+    unsigned *flag;
     __device__ __forceinline__ void put(const Site &w, int p, float g, float) const
     {
-        __stcs(f + (long long)p * P + w.cell, g);
+        const long long i = (long long)p * P + w.cell;
+        if (in_bounds(i, n, flag)) __stcs(f + i, g);
     }
     __device__ __forceinline__ void put(const Site &w, int p, float2 g, float2) const
     {
-        float *q = f + (long long)p * P + w.cell;  // x even: 8-byte aligned
+        const long long i = (long long)p * P + w.cell;
+        if (!in_bounds(i, n - (w.two ? 1 : 0), flag)) return;
+        float *q = f + i;  // x even: 8-byte aligned
         if (w.two)
             __stcs(reinterpret_cast<float2 *>(q), g);
         else
@@ -954,7 +984,10 @@ __global__ void __launch_bounds__(256)
     t.base = fin + (long long)(y + GY) * c.pitch + (x + GX);
     t.P = c.plane;
     t.py = c.pitch;
-    StateOut o{fout, c.plane, c.nx, c.ny, c.pitch};
+    t.lo = fin;
+    t.n = (long long)S * Q * c.plane;
+    t.flag = flag;
+    StateOut o{fout, c.plane, c.nx, c.ny, c.pitch, (long long)S * Q * c.plane, flag};
     step_cell<S>(c, c, t, x, y, true, o, flag);
 }
 
@@ -1063,7 +1096,7 @@ __device__ __forceinline__ HaloSides halo_sides(int bx0, int by0, int nx, int ny
 template <int NP, int TX, int TY, int NT>
 __device__ __forceinline__ void halo_load(HaloRegs<NP, TX, TY, NT> &hr, const HaloSides &hs,
                                           const float *__restrict__ fin, int bx0, int by0, int nx, int ny,
-                                          int pitch, long long plane, int bc_x, int bc_y, int tid)
+                                          int pitch, long long plane, int bc_x, int bc_y, int tid, unsigned *flag)
 {
     using H = HaloRegs<NP, TX, TY, NT>;
     const long long base = (long long)GY * pitch + GX;
@@ -1078,7 +1111,8 @@ __device__ __forceinline__ void halo_load(HaloRegs<NP, TX, TY, NT> &hr, const Ha
             const int y = by0 + r;
             if (it < H::XI && j < need && y < hs.y_hi) {
                 const int xs = halo_source(side == 0 ? j - 2 : nx + j, nx, bc_x);
-                hr.x[side][k] = fin[p * plane + base + (long long)y * pitch + xs];
+                const long long i = p * plane + base + (long long)y * pitch + xs;
+                if (in_bounds(i, NP * plane, flag)) hr.x[side][k] = fin[i];
             }
         }
     }
@@ -1093,7 +1127,8 @@ __device__ __forceinline__ void halo_load(HaloRegs<NP, TX, TY, NT> &hr, const Ha
             const int x = bx0 + c;
             if (it < H::YI && j < need && x < hs.x_hi) {
                 const int ys = halo_source(side == 0 ? j - 2 : ny + j, ny, bc_y);
-                hr.y[side][k] = fin[p * plane + base + (long long)ys * pitch + x];
+                const long long i = p * plane + base + (long long)ys * pitch + x;
+                if (in_bounds(i, NP * plane, flag)) hr.y[side][k] = fin[i];
             }
         }
     }
@@ -1107,7 +1142,7 @@ __device__ __forceinline__ void halo_load(HaloRegs<NP, TX, TY, NT> &hr, const Ha
 template <int NP, int TX, int TY, int NT>
 __device__ __forceinline__ void halo_fill(const HaloSides &hs, float *tile, const float *__restrict__ fin, int bx0,
                                           int by0, int nx, int ny, int pitch, long long plane, int bc_x, int bc_y,
-                                          int tid)
+                                          int tid, unsigned *flag)
 {
     using H = HaloRegs<NP, TX, TY, NT>;
     constexpr int BX = TX + 8, PS = (TY + 4) * BX;
@@ -1120,8 +1155,9 @@ __device__ __forceinline__ void halo_fill(const HaloSides &hs, float *tile, cons
             const int y = by0 + r;
             if (j >= need || y >= hs.y_hi) continue;
             const int xg = side == 0 ? j - 2 : nx + j;
-            tile[p * PS + (r + 2) * BX + (xg - bx0 + 4)] =
-                fin[p * plane + base + (long long)y * pitch + halo_source(xg, nx, bc_x)];
+            const long long i = p * plane + base + (long long)y * pitch + halo_source(xg, nx, bc_x);
+            const int t = p * PS + (r + 2) * BX + (xg - bx0 + 4);
+            if (in_bounds(i, NP * plane, flag) && in_bounds(t, NP * PS, flag)) tile[t] = fin[i];
         }
     }
     for (int side = 0; side < 2; ++side) {
@@ -1132,8 +1168,9 @@ __device__ __forceinline__ void halo_fill(const HaloSides &hs, float *tile, cons
             const int x = bx0 + c;
             if (j >= need || x >= hs.x_hi) continue;
             const int yg = side == 0 ? j - 2 : ny + j;
-            tile[p * PS + (yg - by0 + 2) * BX + (c + 4)] =
-                fin[p * plane + base + (long long)halo_source(yg, ny, bc_y) * pitch + x];
+            const long long i = p * plane + base + (long long)halo_source(yg, ny, bc_y) * pitch + x;
+            const int t = p * PS + (yg - by0 + 2) * BX + (c + 4);
+            if (in_bounds(i, NP * plane, flag) && in_bounds(t, NP * PS, flag)) tile[t] = fin[i];
         }
     }
     __syncthreads();
@@ -1143,7 +1180,7 @@ __device__ __forceinline__ void halo_fill(const HaloSides &hs, float *tile, cons
 // threads of the CTA call this for a boundary tile.
 template <int NP, int TX, int TY, int NT>
 __device__ __forceinline__ void halo_store(const HaloRegs<NP, TX, TY, NT> &hr, const HaloSides &hs, float *tile,
-                                           int bx0, int by0, int nx, int ny, int tid)
+                                           int bx0, int by0, int nx, int ny, int tid, unsigned *flag)
 {
     using H = HaloRegs<NP, TX, TY, NT>;
     constexpr int BX = TX + 8, PS = (TY + 4) * BX;
@@ -1157,7 +1194,8 @@ __device__ __forceinline__ void halo_store(const HaloRegs<NP, TX, TY, NT> &hr, c
             const int j = it & 1, r = (it >> 1) % TY, p = (it >> 1) / TY;
             if (it < H::XI && j < need && by0 + r < hs.y_hi) {
                 const int xg = side == 0 ? j - 2 : nx + j;
-                tile[p * PS + (r + 2) * BX + (xg - bx0 + 4)] = hr.x[side][k];
+                const int t = p * PS + (r + 2) * BX + (xg - bx0 + 4);
+                if (in_bounds(t, NP * PS, flag)) tile[t] = hr.x[side][k];
             }
         }
     }
@@ -1171,7 +1209,8 @@ __device__ __forceinline__ void halo_store(const HaloRegs<NP, TX, TY, NT> &hr, c
             const int c = it % TX, j = (it / TX) & 1, p = it / (2 * TX);
             if (it < H::YI && j < need && bx0 + c < hs.x_hi) {
                 const int yg = side == 0 ? j - 2 : ny + j;
-                tile[p * PS + (yg - by0 + 2) * BX + (c + 4)] = hr.y[side][k];
+                const int t = p * PS + (yg - by0 + 2) * BX + (c + 4);
+                if (in_bounds(t, NP * PS, flag)) tile[t] = hr.y[side][k];
             }
         }
     }
@@ -1213,16 +1252,17 @@ __global__ void __launch_bounds__(TX / CW * TY, tma_ctas_per_sm(S, TX, TY))
         mbar_wait(b, 0, TMA_WAIT_LIMIT);
         return;
     }
-    if (hs.any()) halo_fill<NP, TX, TY, NT>(hs, tile, fin, bx0, by0, c.nx, c.ny, c.pitch, c.plane, c.bc_x, c.bc_y, tid);
+    if (hs.any())
+        halo_fill<NP, TX, TY, NT>(hs, tile, fin, bx0, by0, c.nx, c.ny, c.pitch, c.plane, c.bc_x, c.bc_y, tid, flag);
     const int x = bx0 + CW * tx, y = by0 + ty;
     if (x >= c.nx || y >= c.ny) return;
-    StateOutNoImages o{fout, c.plane};
+    StateOutNoImages o{fout, c.plane, (long long)NP * c.plane, flag};
     const float *base = tile + (ty + 2) * BX + (CW * tx + 4);
     if constexpr (CW == 2) {
-        const SmemTile2 t{base, BY * BX, BX};
+        const SmemTile2 t{base, BY * BX, BX, tile, NP * BY * BX, flag};
         step_cell<S>(c, c, t, x, y, x + 1 < c.nx, o, flag, xa);
     } else {
-        const SmemTile t{base, BY * BX, BX};
+        const SmemTile t{base, BY * BX, BX, tile, NP * BY * BX, flag};
         step_cell<S>(c, c, t, x, y, true, o, flag, xa);
     }
 }

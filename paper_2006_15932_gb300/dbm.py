@@ -15,7 +15,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libdbm.so")
+# DBM_LIB selects another build of the library (e.g. the bounds-checked one)
+LIB_PATH = os.environ.get("DBM_LIB") or os.path.join(HERE, "_build", "libdbm.so")
 
 Q = 16
 MAX_SPECIES = 8
@@ -33,6 +34,7 @@ ERRORS = {
     -6: "DBM_ERR_NEGATIVE",
     -7: "DBM_ERR_STABILITY",
     -8: "DBM_ERR_TIMEOUT",
+    -9: "DBM_ERR_BOUNDS",
 }
 KERNELS = {"auto": 0, "generic": 1, "tma": 2, "tma_cell": 3, "tma_pair": 4}
 THERMO = {"floatfloat": 0, "fp64": 1}

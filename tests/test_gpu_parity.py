@@ -442,3 +442,40 @@ def test_bf16dev_conservation(D, orc):
     c1 = s.conservation().cpu().numpy()
     assert np.max(np.abs(c1[:2] - c0[:2]) / np.abs(c0[:2])) < 1e-5
     assert abs(c1[4] - c0[4]) / abs(c0[4]) < 1e-5
+
+
+@pytest.mark.parametrize("prec,ns", [("fp32", 2), ("fp32", 1), ("fp64", 3), ("bf16dev", 2)])
+def test_page_locked_host_fields(D, prec, ns):
+    """dbm_set_state from page-locked host fields, and dbm_moments,
+    dbm_conservation and dbm_get_f into page-locked host memory, give the
+    bits of the same calls on device arrays: staged through the free state
+    buffer where it is large enough (two species FP32, FP64), read or
+    written in place otherwise (one species FP32 moments, BF16DEV moments);
+    the staging leaves the state alone (the runs stay equal step after
+    step)."""
+    pb = W.random_smooth(45, 19, ns, seed=8)
+    a, b = D.Solver(pb, prec), D.Solver(pb, prec)
+    fields = [np.ascontiguousarray(x, dtype=np.float64) for x in (pb.rho_s, pb.ux, pb.uy, pb.T)]
+    dev = [torch.from_numpy(x).to(a.device) for x in fields]
+    host = [torch.from_numpy(x.copy()).pin_memory() for x in fields]
+    D.dbm_set_state(a.h, *[t.data_ptr() for t in dev], a._st())
+    D.dbm_set_state(b.h, *[t.data_ptr() for t in host], b._st())
+    for rnd in range(2):
+        a.step(3)
+        b.step(3)
+        ma = a.moments().cpu().numpy()
+        mh = torch.empty(ma.shape, dtype=torch.float64).pin_memory()
+        D.dbm_moments(b.h, mh.data_ptr(), b._st())
+        ca = a.conservation().cpu().numpy()
+        ch = torch.empty(ca.shape, dtype=torch.float64).pin_memory()
+        D.dbm_conservation(b.h, ch.data_ptr(), b._st())
+        fa = a.get_f().cpu().numpy()
+        fh = torch.empty(fa.shape, dtype=torch.float64).pin_memory()
+        D.dbm_get_f(b.h, fh.data_ptr(), b._st())
+        torch.cuda.synchronize()
+        assert np.array_equal(mh.numpy(), ma), rnd
+        assert np.array_equal(ch.numpy(), ca), rnd
+        assert np.array_equal(fh.numpy(), fa), rnd
+    assert a.status() == (0, 0) and b.status() == (0, 0)
+    a.close()
+    b.close()
