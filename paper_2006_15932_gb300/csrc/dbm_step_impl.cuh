@@ -323,30 +323,6 @@ __device__ __forceinline__ V feq_of(int i, const V o[16])
                     : vsub(vsub(A, H), vsub(Y, X));
 }
 
-// f^eq of velocity i from the block solution, for one cell, formed exactly
-// in float-float and rounded stochastically with the uniform number u (the
-// stochastic mode: a round-to-nearest assembly biases the mass and energy
-// of the equilibrium where the vector parts are not small next to the ring
-// means, since the roundings of a mirrored pair then no longer cancel).
-__device__ __forceinline__ float feq_of_sr(int i, const float o[16], float u)
-{
-    const int r = i >> 2, k = i & 3;
-    const float A = o[r], X = o[8 + r], Y = o[12 + r];
-    float e1, e2, e3 = 0.0f;
-    float s1, v;
-    if ((r & 1) == 0) {
-        const float B = o[4 + (r >> 1)];
-        s1 = ff_sum(A, (k & 1) ? -B : B, e1);  // A + B on +-x, A - B on +-y
-        v = k == 0 ? X : k == 1 ? Y : k == 2 ? -X : -Y;
-    } else {
-        const float H = o[6 + (r >> 1)];
-        s1 = ff_sum(A, (k & 1) ? -H : H, e1);
-        v = ff_sum(k == 0 ? X : k == 1 ? Y : k == 2 ? -X : -Y, k == 0 ? Y : k == 1 ? -X : k == 2 ? -Y : X, e3);
-    }
-    const float s2 = ff_sum(s1, v, e2);
-    return sr_ff(s2, __fadd_rn(__fadd_rn(e1, e2), e3), u);
-}
-
 // NND flux difference along one axis for a velocity component of sign
 // `sgn` (+1 or -1): (H_{j+1/2} - H_{j-1/2}) / c, from f_{j-2..j+2}.
 //   c > 0: H_{j+1/2} = c [f_j + mm(f_j - f_{j-1}, f_{j+1} - f_j)/2]
@@ -941,16 +917,9 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
             // 6. forward Euler: f + dt/tau (f^eq,tot - f) - dt v . grad f,
             // with the 5. NND advection terms of x and y each applied as one
             // fused multiply-add (no product is left for the compiler to fuse)
-            V e = feq_of<V>(i, o);
+            const V e = feq_of<V>(i, o);
             if constexpr (X::on) {
                 if (sr) {  // the increment, then one stochastically rounded sum
-#pragma unroll
-                    for (int j = 0; j < L::n; ++j) {
-                        float oj[16];
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) oj[q] = L::get(o[q], j);
-                        L::set(e, j, feq_of_sr(i, oj, sr_uniform(hcell[j], S * Q + 1 + 7 * S + p)));
-                    }
                     V d = vmul(dtt, vsub(e, f0[i]));
                     if (dir_x(i) > 0)
                         d = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos<V>(t.ld(p, -2, 0), t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0)),
