@@ -123,14 +123,24 @@ enum dbm_health_bits {
  * same explicitly rounded arithmetic and gives bitwise identical results;
  * they differ in speed only. */
 enum dbm_step_kernel {
-    DBM_KERNEL_AUTO = 0,      /* TMA-staged where built (FP32, S <= 4), else generic;
-                                 tile as DBM_KERNEL_TMA                              */
+    DBM_KERNEL_AUTO = 0,      /* TMA-staged where built (FP32), else generic; tile as
+                                 DBM_KERNEL_TMA                                      */
     DBM_KERNEL_GENERIC = 1,   /* stencil read from global memory                      */
-    DBM_KERNEL_TMA = 2,       /* tile + halo staged in shared memory by one TMA copy;
-                                 for S = 2 two cells per thread on grids of at least
-                                 4096 tiles of 64 x 8 cells, else one cell per thread */
-    DBM_KERNEL_TMA_CELL = 3,  /* TMA-staged, one cell per thread                      */
-    DBM_KERNEL_TMA_PAIR = 4   /* TMA-staged, two adjacent cells per thread (S = 2)    */
+    DBM_KERNEL_TMA = 2,       /* tile + halo staged in shared memory by TMA copies:
+                                 S = 1: one cell per thread; S = 2: all planes in one
+                                 copy, two cells per thread on grids of at least 4096
+                                 tiles of 64 x 8 cells, else one cell per thread;
+                                 S >= 3: as DBM_KERNEL_TMA_STAGED (with the thermo or
+                                 rounding option: one cell per thread, S <= 4)       */
+    DBM_KERNEL_TMA_CELL = 3,  /* TMA-staged, all planes in one copy, one cell per
+                                 thread (S <= 4)                                     */
+    DBM_KERNEL_TMA_PAIR = 4,  /* TMA-staged, two adjacent cells per thread: S = 2 all
+                                 planes in one copy, S >= 3 species-staged           */
+    DBM_KERNEL_TMA_STAGED = 5 /* TMA-staged one species at a time through two shared-
+                                 memory buffers (each species copied for its moment
+                                 sums and again for its update), two adjacent cells
+                                 per thread on 64 x 8 tiles; 2 <= S <= 8, without the
+                                 thermo and rounding options                         */
 };
 
 /* Constants of one species sigma. */

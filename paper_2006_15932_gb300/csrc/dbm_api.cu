@@ -262,10 +262,20 @@ static int validate(dbm_handle *h, const dbm_params &p)
     }
     if (p.precision != DBM_FP64 && p.precision != DBM_FP32 && p.precision != DBM_BF16DEV)
         return fail(h, DBM_ERR_INVALID, "unknown precision %d", p.precision);
-    if (p.step_kernel < DBM_KERNEL_AUTO || p.step_kernel > DBM_KERNEL_TMA_PAIR)
+    if (p.step_kernel < DBM_KERNEL_AUTO || p.step_kernel > DBM_KERNEL_TMA_STAGED)
         return fail(h, DBM_ERR_INVALID, "unknown step kernel %d", p.step_kernel);
-    if (p.step_kernel == DBM_KERNEL_TMA_PAIR && (p.precision != DBM_FP32 || p.nspecies != 2))
-        return fail(h, DBM_ERR_INVALID, "the two-cells-per-thread step is built for FP32 with two species");
+    const bool options = p.thermo != DBM_THERMO_FLOATFLOAT || p.rounding != DBM_ROUND_NEAREST;
+    if (p.step_kernel == DBM_KERNEL_TMA_PAIR &&
+        (p.precision != DBM_FP32 || p.nspecies < 2 || (p.nspecies > 2 && options)))
+        return fail(h, DBM_ERR_INVALID,
+                    "the two-cells-per-thread step is built for FP32 with two or more species "
+                    "(with the thermo or rounding option: two species)");
+    if (p.step_kernel == DBM_KERNEL_TMA_STAGED && (p.precision != DBM_FP32 || p.nspecies < 2 || options))
+        return fail(h, DBM_ERR_INVALID,
+                    "the species-staged step is built for FP32 with two or more species, without the thermo "
+                    "and rounding options");
+    if (p.step_kernel == DBM_KERNEL_TMA_CELL && p.nspecies > 4)
+        return fail(h, DBM_ERR_INVALID, "the one-cell TMA-staged step is built for up to four species");
     const bool tma_kind = p.step_kernel != DBM_KERNEL_AUTO && p.step_kernel != DBM_KERNEL_GENERIC;
     if (p.precision == DBM_BF16DEV &&
         (p.nspecies > 4 || p.k_ov != 0.0 || p.accel[0] != 0.0 || p.accel[1] != 0.0 || tma_kind))
@@ -475,7 +485,7 @@ int dbm_bind(dbm_handle *h, void *f_a, void *f_b, void *scratch)
     const int want = h->p.step_kernel;
     if ((want != DBM_KERNEL_AUTO && want != DBM_KERNEL_GENERIC) || uses_acc(h->p))
         if (!h->tma_ok)
-            return fail(h, DBM_ERR_INVALID, "the TMA-staged step kernel is built for FP32 with at most 4 species");
+            return fail(h, DBM_ERR_INVALID, "no TMA-staged step kernel for these parameters");
     return DBM_OK;
 }
 

@@ -104,6 +104,7 @@ struct dbm_handle {
     int tma_ok;           // the TMA-staged step kernel can run
     int tma_tx, tma_ty;   // its tile (cells) and cells per thread (1 or 2),
     int tma_cw;           // fixed at dbm_bind
+    int tma_staged;       // the species-staged step (one species per copy)
     double cinv[DBM_MAX_SPECIES][16][16];  // host FP64 M^-1 per species
     double eqA[DBM_MAX_SPECIES][4][4];     // symmetry blocks of M^-1
     double eqB[DBM_MAX_SPECIES][2][2];
@@ -147,6 +148,18 @@ namespace dbm {
 constexpr int tma_tile_x(int S) { return S == 1 ? 64 : 32; }
 constexpr int tma_tile_y(int S) { return S == 1 ? 4 : S == 2 ? 7 : S == 3 ? 8 : 6; }
 constexpr int PAIR_TX = 64, PAIR_TY = 8;
+// The species-staged step (two cells per thread, the tile passing through
+// shared memory one species at a time in two buffers; k_step_staged): its
+// tile, 64 x 8 cells in two buffers of 55 KB, two CTAs of 256 threads per
+// SM.  A build may set another with -DDBM_STAGED_TX=.. -DDBM_STAGED_TY=..
+// (TX a multiple of 8).
+#ifndef DBM_STAGED_TX
+#define DBM_STAGED_TX 64
+#endif
+#ifndef DBM_STAGED_TY
+#define DBM_STAGED_TY 8
+#endif
+constexpr int STAGED_TX = DBM_STAGED_TX, STAGED_TY = DBM_STAGED_TY;
 constexpr long long PAIR_MIN_TILES = 4096;
 
 // CTAs of a TX x TY tile kernel that fit on one SM at once, limited by

@@ -12,6 +12,23 @@ template <int S>
 int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st);
 template <int S, int TX, int TY, int CW, bool ACC>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st);
+template <int S, int TX, int TY>
+int launch_step_staged_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st);
+
+// The species-staged step of the handle's tile (no arithmetic options).
+static int launch_staged(dbm_handle *h, const CUtensorMap *tm, const void *fin, void *fout, cudaStream_t st)
+{
+    switch (h->p.nspecies) {
+    case 2: return launch_step_staged_t<2, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
+    case 3: return launch_step_staged_t<3, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
+    case 4: return launch_step_staged_t<4, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
+    case 5: return launch_step_staged_t<5, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
+    case 6: return launch_step_staged_t<6, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
+    case 7: return launch_step_staged_t<7, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
+    case 8: return launch_step_staged_t<8, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
+    }
+    return DBM_ERR_INVALID;
+}
 
 // The TMA-staged step of the handle's tile, with (ACC) or without the FP32
 // arithmetic options.
@@ -29,18 +46,38 @@ static int launch_tma(dbm_handle *h, const CUtensorMap *tm, const void *fin, voi
     return DBM_ERR_INVALID;
 }
 
+// The all-species TMA-staged kernels exist for FP32 with up to four species;
+// the species-staged one for two to eight species without the arithmetic
+// options.
 bool tma_supported(const dbm_params &p) { return p.precision == DBM_FP32 && p.nspecies <= 4; }
+static bool staged_supported(const dbm_params &p)
+{
+    return p.precision == DBM_FP32 && p.nspecies >= 2 && p.nspecies <= DBM_MAX_SPECIES && !uses_acc(p);
+}
 
-// The tile of the TMA-staged step: two cells per thread for two species
-// when asked for, or (DBM_KERNEL_AUTO / DBM_KERNEL_TMA) on grids of at least
-// PAIR_MIN_TILES pair tiles; else the species count's one-cell tile.
+// The tile of the TMA-staged step.  Two species: two cells per thread when
+// asked for, or (DBM_KERNEL_AUTO / DBM_KERNEL_TMA) on grids of at least
+// PAIR_MIN_TILES pair tiles, else the one-cell tile; the species-staged
+// kernel only when asked for.  Three or more species: the species-staged
+// kernel (two cells per thread) unless one cell per thread is asked for or
+// the arithmetic options are on (one-cell kernels, up to four species).
 static void choose_tile(dbm_handle *h)
 {
     const dbm_params &p = h->p;
+    const int want = p.step_kernel;
+    h->tma_staged = 0;
+    if (staged_supported(p) &&
+        (want == DBM_KERNEL_TMA_STAGED || (p.nspecies >= 3 && want != DBM_KERNEL_TMA_CELL))) {
+        h->tma_staged = 1;
+        h->tma_tx = STAGED_TX;
+        h->tma_ty = STAGED_TY;
+        h->tma_cw = 2;
+        return;
+    }
     bool pair = false;
-    if (p.nspecies == 2 && p.step_kernel != DBM_KERNEL_TMA_CELL) {
+    if (p.nspecies == 2 && want != DBM_KERNEL_TMA_CELL) {
         const long long tiles = (long long)((p.nx + PAIR_TX - 1) / PAIR_TX) * ((p.ny + PAIR_TY - 1) / PAIR_TY);
-        pair = p.step_kernel == DBM_KERNEL_TMA_PAIR || tiles >= PAIR_MIN_TILES;
+        pair = want == DBM_KERNEL_TMA_PAIR || tiles >= PAIR_MIN_TILES;
     }
     h->tma_tx = pair ? PAIR_TX : tma_tile_x(p.nspecies);
     h->tma_ty = pair ? PAIR_TY : tma_tile_y(p.nspecies);
@@ -57,8 +94,8 @@ typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32
 int make_tensor_maps(dbm_handle *h)
 {
     h->tma_ok = 0;
-    h->tma_tx = h->tma_ty = h->tma_cw = 0;
-    if (!tma_supported(h->p)) return DBM_OK;
+    h->tma_tx = h->tma_ty = h->tma_cw = h->tma_staged = 0;
+    if (!tma_supported(h->p) && !staged_supported(h->p)) return DBM_OK;
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
@@ -71,14 +108,21 @@ int make_tensor_maps(dbm_handle *h)
     cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)(16 * h->p.nspecies)};
     cuuint64_t strides[2] = {(cuuint64_t)L.pitch * 4, (cuuint64_t)L.plane * 4};
     choose_tile(h);
-    cuuint32_t box[3] = {(cuuint32_t)(h->tma_tx + 8), (cuuint32_t)(h->tma_ty + 4), (cuuint32_t)(16 * h->p.nspecies)};
+    if (!h->tma_staged && !tma_supported(h->p)) {  // no all-species kernel for this species count
+        h->tma_tx = h->tma_ty = h->tma_cw = 0;
+        return DBM_OK;
+    }
+    // the box: the tile, its halo and every plane (one species' planes for
+    // the species-staged kernel)
+    const cuuint32_t planes = (cuuint32_t)(h->tma_staged ? Q : Q * h->p.nspecies);
+    cuuint32_t box[3] = {(cuuint32_t)(h->tma_tx + 8), (cuuint32_t)(h->tma_ty + 4), planes};
     cuuint32_t estr[3] = {1, 1, 1};
     for (int k = 0; k < 2; ++k) {
         CUresult r = encode(&h->tmap[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->f[k], dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
-            h->tma_tx = h->tma_ty = h->tma_cw = 0;
+            h->tma_tx = h->tma_ty = h->tma_cw = h->tma_staged = 0;
             return DBM_OK;
         }
     }
@@ -108,6 +152,7 @@ int launch_step(dbm_handle *h, int cur, cudaStream_t st)
     const int want = h->p.step_kernel;
     if (h->tma_ok && want != DBM_KERNEL_GENERIC) {
         const CUtensorMap *tm = &h->tmap[cur];
+        if (h->tma_staged) return launch_staged(h, tm, fin, fout, st);
         return uses_acc(h->p) ? launch_tma<true>(h, tm, fin, fout, st) : launch_tma<false>(h, tm, fin, fout, st);
     }
     if (uses_acc(h->p)) return DBM_ERR_INVALID;  // the options exist in the TMA-staged kernel only

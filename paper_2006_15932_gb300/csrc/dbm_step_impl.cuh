@@ -196,6 +196,27 @@ struct SmemTile2 {
     }
 };
 
+// A tile that passes through shared memory one species at a time
+// (StagedTile2, the species-staged step) declares kStaged; step_cell then
+// brackets the reads of each species with acquire / release and reads
+// through view(k, s), the buffer of use k.  Other tiles hold every species
+// at once and are read as they are.
+template <class T, class = void>
+struct is_staged : std::false_type {
+};
+template <class T>
+struct is_staged<T, std::void_t<decltype(T::kStaged)>> : std::true_type {
+};
+
+template <class Tile>
+__device__ __forceinline__ decltype(auto) stage_view(const Tile &t, int k, int s)
+{
+    if constexpr (is_staged<Tile>::value)
+        return t.view(k, s);
+    else
+        return (t);
+}
+
 // The 16 combinations of f-hat that feed the symmetry blocks, for one cell:
 // c[0..3] ring-mean system, c[4..5] B system, c[6..7] H system,
 // c[8..11] x-vector system, c[12..15] y-vector system.  Each is returned as
@@ -636,15 +657,20 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
         sr = xa.stochastic != 0;
     }
 
+    constexpr bool kStaged = is_staged<Tile>::value;
+    static_assert(!(kStaged && X::on), "the arithmetic options read every species at once");
+
     // 1. species moments, by ring sums
     V n[S], nf = bc<V>(0.0f), no = bc<V>(0.0f), cap, w, wx, wy, we, wd;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
+        if constexpr (kStaged) t.acquire(s);
+        const auto &ts = stage_view(t, s, s);
         V sn, sx, sy, se;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const V f0 = t.ld(s * Q + 4 * r, 0, 0), f1 = t.ld(s * Q + 4 * r + 1, 0, 0);
-            const V f2 = t.ld(s * Q + 4 * r + 2, 0, 0), f3 = t.ld(s * Q + 4 * r + 3, 0, 0);
+            const V f0 = ts.ld(s * Q + 4 * r, 0, 0), f1 = ts.ld(s * Q + 4 * r + 1, 0, 0);
+            const V f2 = ts.ld(s * Q + 4 * r + 2, 0, 0), f3 = ts.ld(s * Q + 4 * r + 3, 0, 0);
             const V rs = vadd(vadd(f0, f2), vadd(f1, f3));
             V rx, ry;
             if ((r & 1) == 0) {
@@ -667,6 +693,7 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
                 se = vfma(bc<V>(c.qr[s][r]), rs, se);
             }
         }
+        if constexpr (kStaged) t.release(s);
         n[s] = sn;
         if (s == g.fuel) nf = sn;  // selects, no runtime-indexed register array
         if (s == g.oxid) no = sn;
@@ -801,9 +828,11 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
     // slower unrolled)
 #pragma unroll(S <= 3 ? S : 1)
     for (int s = 0; s < S; ++s) {
+        if constexpr (kStaged) t.acquire(S + s);
+        const auto &ts = stage_view(t, S + s, s);
         V f0[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) f0[i] = t.ld(s * Q + i, 0, 0);
+        for (int i = 0; i < Q; ++i) f0[i] = ts.ld(s * Q + i, 0, 0);
         // species density from step 1 (selected, not indexed)
         V ns = n[0];
 #pragma unroll
@@ -922,16 +951,16 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
                 if (sr) {  // the increment, then one stochastically rounded sum
                     V d = vmul(dtt, vsub(e, f0[i]));
                     if (dir_x(i) > 0)
-                        d = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos<V>(t.ld(p, -2, 0), t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0)),
+                        d = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos<V>(ts.ld(p, -2, 0), ts.ld(p, -1, 0), f0[i], ts.ld(p, 1, 0)),
                                  d);
                     else if (dir_x(i) < 0)
-                        d = vfma(bc<V>(c.cdx[s][r]), nnd_diff_neg<V>(t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0), t.ld(p, 2, 0)),
+                        d = vfma(bc<V>(c.cdx[s][r]), nnd_diff_neg<V>(ts.ld(p, -1, 0), f0[i], ts.ld(p, 1, 0), ts.ld(p, 2, 0)),
                                  d);
                     if (dir_y(i) > 0)
-                        d = vfma(bc<V>(-c.cdy[s][r]), nnd_diff_pos<V>(t.ld(p, 0, -2), t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1)),
+                        d = vfma(bc<V>(-c.cdy[s][r]), nnd_diff_pos<V>(ts.ld(p, 0, -2), ts.ld(p, 0, -1), f0[i], ts.ld(p, 0, 1)),
                                  d);
                     else if (dir_y(i) < 0)
-                        d = vfma(bc<V>(c.cdy[s][r]), nnd_diff_neg<V>(t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1), t.ld(p, 0, 2)),
+                        d = vfma(bc<V>(c.cdy[s][r]), nnd_diff_neg<V>(ts.ld(p, 0, -1), f0[i], ts.ld(p, 0, 1), ts.ld(p, 0, 2)),
                                  d);
                     V f1;
 #pragma unroll
@@ -944,28 +973,29 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
             V f1 = vfma(dtt, vsub(e, f0[i]), f0[i]);
             if constexpr (L::n == 2) {
                 if (dir_x(i) != 0) {
-                    const V a = t.ld(p, -2, 0), b = t.ld(p, 2, 0);
+                    const V a = ts.ld(p, -2, 0), b = ts.ld(p, 2, 0);
                     if (dir_x(i) > 0)
                         f1 = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos_pair(a, f0[i], b), f1);
                     else
                         f1 = vfma(bc<V>(c.cdx[s][r]), nnd_diff_neg_pair(a, f0[i], b), f1);
                 }
             } else if (dir_x(i) > 0) {
-                f1 = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos<V>(t.ld(p, -2, 0), t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0)),
+                f1 = vfma(bc<V>(-c.cdx[s][r]), nnd_diff_pos<V>(ts.ld(p, -2, 0), ts.ld(p, -1, 0), f0[i], ts.ld(p, 1, 0)),
                           f1);
             } else if (dir_x(i) < 0) {
-                f1 = vfma(bc<V>(c.cdx[s][r]), nnd_diff_neg<V>(t.ld(p, -1, 0), f0[i], t.ld(p, 1, 0), t.ld(p, 2, 0)),
+                f1 = vfma(bc<V>(c.cdx[s][r]), nnd_diff_neg<V>(ts.ld(p, -1, 0), f0[i], ts.ld(p, 1, 0), ts.ld(p, 2, 0)),
                           f1);
             }
             if (dir_y(i) > 0)
-                f1 = vfma(bc<V>(-c.cdy[s][r]), nnd_diff_pos<V>(t.ld(p, 0, -2), t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1)),
+                f1 = vfma(bc<V>(-c.cdy[s][r]), nnd_diff_pos<V>(ts.ld(p, 0, -2), ts.ld(p, 0, -1), f0[i], ts.ld(p, 0, 1)),
                           f1);
             else if (dir_y(i) < 0)
-                f1 = vfma(bc<V>(c.cdy[s][r]), nnd_diff_neg<V>(t.ld(p, 0, -1), f0[i], t.ld(p, 0, 1), t.ld(p, 0, 2)),
+                f1 = vfma(bc<V>(c.cdy[s][r]), nnd_diff_neg<V>(ts.ld(p, 0, -1), f0[i], ts.ld(p, 0, 1), ts.ld(p, 0, 2)),
                           f1);
             out.put(w_, p, f1, e);
         }
         if (images) out.images(w_, s);
+        if constexpr (kStaged) t.release(S + s);
     }
     if (images) out.images_mix(w_);
     if (bad) raise_flag(flag, bad);
@@ -1026,15 +1056,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long lo
 constexpr long long TMA_WAIT_LIMIT = TMA_WAIT_POLLS;  // drain wait: try_wait polls (each may suspend ~us)
 
 // Issue the tile copy (leader thread): box origin column bx0 (= bx0 + GX - 4),
-// row by0 (= by0 + GY - 2), plane 0.
+// row by0 (= by0 + GY - 2), plane z.
 __device__ __forceinline__ void tma_tile_load(float *tile, unsigned long long tmap, int bx0, int by0,
-                                              unsigned bar, unsigned bytes)
+                                              unsigned bar, unsigned bytes, int z = 0)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(tile)),
-        "l"(tmap), "r"(bx0), "r"(by0), "r"(0), "r"(bar)
+        "l"(tmap), "r"(bx0), "r"(by0), "r"(z), "r"(bar)
         : "memory");
 }
 
@@ -1300,6 +1330,176 @@ int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, v
     k_step_tma<S, TX, TY, CW, X><<<grid, block, smem, st>>>(c, *tmap, (const float *)fin, (float *)fout,
                                                               (unsigned *)h->scratch, xa);
     return set_cuda_error(h, cudaGetLastError(), "TMA step kernel launch");
+}
+
+
+// ---------------------------------------------------------------------------
+// The species-staged step.  The tile and its radius-2 halo pass through
+// shared memory one species at a time, in two buffers that each hold the Q
+// planes of one species (BX x BY cells), so the shared memory of a CTA does
+// not grow with the species count: three and more species run two cells per
+// thread at two CTAs per SM (the all-species tile of three species in pairs
+// would hold one).  Each species is copied twice per tile: for its moment
+// sums (step 1 reads the tile's own cells) and for its update (the
+// stencil).  Use k = 0 .. 2S-1 takes species k mod S from buffer k & 1,
+// whose mbarrier completes its phase k >> 1 with that copy; while a use is
+// computed the copy of the next one is in flight, and once every thread is
+// done with a buffer (the barrier in release) the leader refills it for use
+// k + 2.  A tile at the domain boundary fills each copy's halo from the
+// interior of the input (halo_fill on that species' planes).
+//
+// Waits are bounded.  The first one takes c.wait_polls polls (a test can
+// make it run out); a wait that runs out raises DBM_HEALTH_TIMEOUT, and the
+// first one then waits once more, with the full limit.  A thread whose wait
+// ran out for good stops waiting, the leader stops issuing copies, and at
+// the end the leader waits (bounded) for the copies it left in flight.
+template <int S, int TX, int TY>
+struct StagedTile2 {
+    static constexpr bool kStaged = true;
+    static constexpr int BX = TX + 8, BY = TY + 4, PS = BX * BY, NT = TX / 2 * TY;
+    static constexpr unsigned BYTES = (unsigned)(PS * Q * sizeof(float));
+    using V = float2;
+    float *buf;         // buffer 0 (buffer 1 follows at Q * PS)
+    const float *cell;  // buffer 0, plane 0, this thread's row and first column
+    unsigned long long tmap;
+    unsigned bar0;      // mbarrier of buffer 0 (buffer 1: bar0 + 8)
+    const float *fin;
+    int bx0, by0, nx, ny, pitch, bc_x, bc_y, wait_polls;
+    long long plane;
+    unsigned *flag;
+    mutable int failed_at;  // the use whose wait ran out for good; 2S: none
+
+    // view of use k: plane s * Q + i of species s read from buffer k & 1
+    __device__ __forceinline__ SmemTile2 view(int k, int s) const
+    {
+        return SmemTile2{cell + ((k & 1) - s) * Q * PS, PS, BX, buf, 2 * Q * PS, flag};
+    }
+    __device__ __forceinline__ static bool leader() { return threadIdx.x == 0 && threadIdx.y == 0; }
+    // leader: the copy of use k into its buffer
+    __device__ __forceinline__ void issue(int k) const
+    {
+        tma_tile_load(buf + (k & 1) * Q * PS, tmap, bx0, by0, bar0 + 8u * (k & 1), BYTES, (k % S) * Q);
+    }
+    __device__ __forceinline__ void acquire(int k) const
+    {
+        if (failed_at == 2 * S) {
+            const unsigned bar = bar0 + 8u * (k & 1), par = (k >> 1) & 1;
+            bool ok = mbar_wait(bar, par, k == 0 ? wait_polls : TMA_WAIT_LIMIT);
+            if (!ok) {
+                raise_flag(flag, DBM_HEALTH_TIMEOUT);
+                if (k == 0) ok = mbar_wait(bar, par, TMA_WAIT_LIMIT);
+                if (!ok) failed_at = k;
+            }
+        }
+        const HaloSides hs = halo_sides<TX, TY>(bx0, by0, nx, ny);
+        if (hs.any())
+            halo_fill<Q, TX, TY, NT>(hs, buf + (k & 1) * Q * PS, fin + (long long)(k % S) * Q * plane, bx0, by0,
+                                     nx, ny, pitch, plane, bc_x, bc_y, threadIdx.y * (TX / 2) + threadIdx.x, flag);
+    }
+    __device__ __forceinline__ void release(int k) const
+    {
+        __syncthreads();  // every thread is done with buffer k & 1
+        if (k + 2 < 2 * S && leader() && failed_at == 2 * S) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(k + 2);
+        }
+    }
+    // leader, after the last use: wait for the copies left in flight by a
+    // wait that ran out (use failed_at and the one after it)
+    __device__ __forceinline__ void drain() const
+    {
+        if (!leader() || failed_at == 2 * S) return;
+        for (int k = failed_at; k < 2 * S && k <= failed_at + 1; ++k)
+            mbar_wait(bar0 + 8u * (k & 1), (k >> 1) & 1, TMA_WAIT_LIMIT);
+    }
+};
+
+constexpr int staged_ctas_per_sm(int TX, int TY)
+{
+    const int by_smem = (227 * 1024) / (2 * (TX + 8) * (TY + 4) * Q * 4 + 1024);
+    return by_smem > 4 ? 4 : by_smem < 1 ? 1 : by_smem;
+}
+
+// Output of the species-staged kernel.  Its barriers are CTA-wide and sit
+// inside the step, so every thread runs the whole step, in the same order
+// of barrier instructions: a thread whose cells lie outside the domain (the
+// ragged edge of a tile) computes on the in-range shared-memory values at
+// its position and stores nothing.
+struct StagedOut : StateOutNoImages {
+    bool live;
+    template <class G>
+    __device__ __forceinline__ void put(const Site &w, int p, G g, G e) const
+    {
+        if (live) StateOutNoImages::put(w, p, g, e);
+    }
+};
+
+template <int S, int TX, int TY>
+__global__ void __launch_bounds__(TX / 2 * TY, staged_ctas_per_sm(TX, TY))
+    k_step_staged(const __grid_constant__ StepConsts<float, S> c, const __grid_constant__ CUtensorMap tmap,
+                  const float *__restrict__ fin, float *__restrict__ fout, unsigned *__restrict__ flag)
+{
+    static_assert(S >= 2 && TX % 8 == 0, "two or more species; 16-byte aligned tile columns");
+    using T = StagedTile2<S, TX, TY>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bars[2];
+    float *buf = reinterpret_cast<float *>(smem_raw);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const unsigned b0 = smem_u32(&bars[0]);
+    if (T::leader()) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0 + 8u) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    const T t{buf,
+              buf + (ty + 2) * T::BX + (2 * tx + 4),
+              reinterpret_cast<unsigned long long>(&tmap),
+              b0,
+              fin,
+              (int)blockIdx.x * TX,
+              (int)blockIdx.y * TY,
+              c.nx,
+              c.ny,
+              c.pitch,
+              c.bc_x,
+              c.bc_y,
+              c.wait_polls,
+              c.plane,
+              flag,
+              2 * S};
+    if (T::leader()) {
+        t.issue(0);
+        t.issue(1);
+    }
+    // every thread steps (see StagedOut); one outside the domain stores
+    // nothing and sends its health bits to a sink
+    __shared__ unsigned health_sink;
+    const int x = t.bx0 + 2 * tx, y = t.by0 + ty;
+    const bool live = x < c.nx && y < c.ny;
+    const StagedOut o{{fout, c.plane, (long long)S * Q * c.plane, flag}, live};
+    step_cell<S>(c, c, t, x, y, live && x + 1 < c.nx, o, live ? flag : &health_sink);
+    t.drain();
+}
+
+template <int S, int TX, int TY>
+int launch_step_staged_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st)
+{
+    constexpr size_t smem = (size_t)2 * (TX + 8) * (TY + 4) * Q * sizeof(float);
+    static bool attr_set = false;  // per instantiation, set once per process
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_staged<S, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return set_cuda_error(h, e, "staged step kernel shared-memory attribute");
+        attr_set = true;
+    }
+    StepConsts<float, S> c;
+    fill_step_consts<float, S>(h, c);
+    dim3 block(TX / 2, TY);
+    dim3 grid((h->p.nx + TX - 1) / TX, (h->p.ny + TY - 1) / TY);
+    k_step_staged<S, TX, TY><<<grid, block, smem, st>>>(c, *tmap, (const float *)fin, (float *)fout,
+                                                         (unsigned *)h->scratch);
+    return set_cuda_error(h, cudaGetLastError(), "staged step kernel launch");
 }
 
 }  // namespace dbm

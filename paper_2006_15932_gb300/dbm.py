@@ -36,7 +36,7 @@ ERRORS = {
     -8: "DBM_ERR_TIMEOUT",
     -9: "DBM_ERR_BOUNDS",
 }
-KERNELS = {"auto": 0, "generic": 1, "tma": 2, "tma_cell": 3, "tma_pair": 4}
+KERNELS = {"auto": 0, "generic": 1, "tma": 2, "tma_cell": 3, "tma_pair": 4, "tma_staged": 5}
 THERMO = {"floatfloat": 0, "fp64": 1}
 ROUNDING = {"nearest": 0, "stochastic": 1}
 EXPORTS = [

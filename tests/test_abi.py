@@ -180,15 +180,24 @@ def _moment_matrix_from_velocities(sp):
 
 
 def test_step_kernel_choices(D):
-    """Unknown kernels, the two-cell step outside FP32 with two species and
-    a TMA kernel for BF16DEV are refused at init; the tile is known only
-    once buffers are bound."""
-    pb2, pb3 = W.random_smooth(8, 8, 2), W.random_smooth(8, 8, 3)
-    for pb, prec, kern in ((pb2, "fp32", 5), (pb2, "fp32", -1), (pb3, "fp32", "tma_pair"),
-                           (pb2, "fp64", "tma_pair"), (pb2, "bf16dev", "tma_cell")):
+    """Unknown kernels, the two-cell steps outside FP32 with two or more
+    species, the one-cell TMA step beyond four species, the species-staged
+    step with an arithmetic option (or the two-cell step for three species
+    with one) and a TMA kernel for BF16DEV are refused at init; the tile is
+    known only once buffers are bound."""
+    pb1, pb2, pb3 = W.random_smooth(8, 8, 1), W.random_smooth(8, 8, 2), W.random_smooth(8, 8, 3)
+    pb5 = W.random_smooth(8, 8, 5)
+    for pb, prec, kern, opts in ((pb2, "fp32", 6, {}), (pb2, "fp32", -1, {}), (pb1, "fp32", "tma_pair", {}),
+                                 (pb1, "fp32", "tma_staged", {}), (pb5, "fp32", "tma_cell", {}),
+                                 (pb2, "fp32", "tma_staged", {"rounding": "stochastic"}),
+                                 (pb3, "fp32", "tma_pair", {"thermo": "fp64"}),
+                                 (pb2, "fp64", "tma_pair", {}), (pb3, "fp64", "tma_staged", {}),
+                                 (pb2, "bf16dev", "tma_cell", {})):
         with pytest.raises(D.DbmError) as e:
-            D.dbm_init(D.params_from_problem(pb, prec, kern))
-        assert e.value.code == -1, (prec, kern)
+            D.dbm_init(D.params_from_problem(pb, prec, kern, **opts))
+        assert e.value.code == -1, (prec, kern, opts)
+    for pb, kern in ((pb3, "tma_pair"), (pb2, "tma_staged"), (pb5, "tma_staged"), (pb2, "tma_pair")):
+        D.dbm_destroy(D.dbm_init(D.params_from_problem(pb, "fp32", kern)))
     h = D.dbm_init(D.params_from_problem(pb2, "fp32", "tma_pair"))
     with pytest.raises(D.DbmError) as e:
         D.dbm_step_tile(h)

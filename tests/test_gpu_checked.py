@@ -3,8 +3,8 @@ memory checker: every index into a shared-memory tile, a state buffer or a
 ghost image is compared with the extent of what it addresses; one outside
 it raises DBM_HEALTH_BOUNDS (bit 32) and the access is skipped.
 
-Small grids with ragged tiles, one- and two-cell tiles, every boundary
-pairing, the generic, FP64 and BF16DEV steps and every batched tile shape
+Small grids with ragged tiles, one- and two-cell tiles, the species-staged
+tile for two to eight species, every boundary pairing, the generic, FP64 and BF16DEV steps and every batched tile shape
 run in a child process on the checked library; no case may raise bit 32,
 and every final state must equal, bit for bit, the same case run on the
 normal library in this process.
@@ -35,6 +35,10 @@ CASES = [  # name, nx, ny, species, precision, kernel, boundaries
     ("four_37x13", 37, 13, 4, "fp32", "auto", PO),
     ("single_70x23", 70, 23, 1, "fp32", "auto", OP),
     ("generic_45x9_s5", 45, 9, 5, "fp32", "generic", PO),
+    ("cell_45x9_s3", 45, 9, 3, "fp32", "tma_cell", PP),
+    ("staged_67x9_s2", 67, 9, 2, "fp32", "tma_staged", OO),
+    ("staged_45x9_s5", 45, 9, 5, "fp32", "auto", PO),
+    ("staged_130x17_s8", 130, 17, 8, "fp32", "auto", OP),
     ("fp64_21x7", 21, 7, 2, "fp64", "auto", OO),
     ("bf16_33x17", 33, 17, 2, "bf16dev", "auto", PO),
     ("bf16_9x5_s1", 9, 5, 1, "bf16dev", "auto", PP),

@@ -1,11 +1,12 @@
 """Failure detection on the GPU without a fault: every bounded wait of the
 TMA-staged steps reports through the health flag when it gives up.
 
-A handle made with dbm_params.wait_polls < 0 polls its tile copy zero times
-before giving up, so each CTA takes the timeout path at once: it raises
-DBM_HEALTH_TIMEOUT, then waits (bounded, with the full limit) for its copy,
-which is valid and lands, and leaves without writing.  Nothing faults or
-hangs; the descriptor and buffers stay valid.  The status call must report
+A handle made with dbm_params.wait_polls < 0 polls its first tile copy zero
+times before giving up, so each CTA takes the timeout path at once: it
+raises DBM_HEALTH_TIMEOUT, then waits (bounded, with the full limit) for its
+copy, which is valid and lands; the all-species kernels then leave without
+writing, the species-staged kernel goes on with its step.  Nothing faults
+or hangs; the descriptor and buffers stay valid.  The status call must report
 DBM_ERR_TIMEOUT with bit 16, and a normal solve afterwards in the same
 context must be green and correct.
 """
@@ -32,7 +33,8 @@ def D():
     return dbm
 
 
-@pytest.mark.parametrize("ns,kernel", [(2, "tma_cell"), (2, "tma_pair"), (3, "tma")])
+@pytest.mark.parametrize("ns,kernel", [(2, "tma_cell"), (2, "tma_pair"), (3, "tma_cell"), (3, "tma"),
+                                       (2, "tma_staged"), (5, "tma")])
 def test_tile_wait_timeout_is_reported(D, orc, ns, kernel):
     pb = W.random_smooth(70, 20, ns, seed=5, reactive=ns == 3)
     s = D.Solver(pb, "fp32", step_kernel=kernel, wait_polls=-1)

@@ -307,19 +307,65 @@ def test_pair_kernel_matches_generic(D, orc, nx, ny, bc, react, force):
 def test_step_tile_choice(D):
     """The handle's tile: two cells per thread for two species on grids of
     at least 4096 tiles of 64 x 8 cells (or when asked for), else one cell
-    per thread; no tile for the generic, FP64 and BF16DEV steps."""
+    per thread; the species-staged 64 x 8 two-cell tile for three or more
+    species (and for two when asked for); one cell per thread for three
+    species with an arithmetic option; no tile for the generic, FP64 and
+    BF16DEV steps."""
     kh = W.kh_shear_layer(2048, ny=1024)
     small = W.kh_shear_layer(1024)
     cases = [(kh, "fp32", "auto", (64, 8, 2)), (kh, "fp32", "tma_cell", (32, 7, 1)),
              (small, "fp32", "auto", (32, 7, 1)), (small, "fp32", "tma_pair", (64, 8, 2)),
              (small, "fp32", "generic", (0, 0, 0)), (small, "fp64", "auto", (0, 0, 0)),
              (small, "bf16dev", "auto", (0, 0, 0)),
-             (W.random_smooth(70, 23, 3), "fp32", "auto", (32, 8, 1)),
+             (W.random_smooth(70, 23, 3), "fp32", "auto", (64, 8, 2)),
+             (W.random_smooth(70, 23, 3), "fp32", "tma_cell", (32, 8, 1)),
+             (W.random_smooth(70, 23, 4), "fp32", "tma_pair", (64, 8, 2)),
+             (W.random_smooth(70, 23, 6), "fp32", "auto", (64, 8, 2)),
+             (small, "fp32", "tma_staged", (64, 8, 2)),
              (W.random_smooth(70, 23, 1), "fp32", "tma", (64, 4, 1))]
     for pb, prec, kern, want in cases:
         s = D.Solver(pb, prec, step_kernel=kern)
         assert s.step_tile() == want, (pb.name, prec, kern)
         s.close()
+    s = D.Solver(W.random_smooth(70, 23, 3), "fp32", step_kernel="tma", thermo="fp64")
+    assert s.step_tile() == (32, 8, 1)
+    s.close()
+
+
+@pytest.mark.parametrize("nx,ny,ns,bc", [(45, 17, 3, (W.PERIODIC, W.OUTFLOW)),
+                                          (130, 19, 3, (W.OUTFLOW, W.PERIODIC)),
+                                          (2, 3, 3, (W.PERIODIC, W.PERIODIC)),
+                                          (129, 8, 2, (W.OUTFLOW, W.OUTFLOW)),
+                                          (1, 1, 2, (W.PERIODIC, W.PERIODIC)),
+                                          (37, 13, 4, (W.PERIODIC, W.OUTFLOW)),
+                                          (64, 16, 4, (W.OUTFLOW, W.OUTFLOW)),
+                                          (67, 9, 5, (W.PERIODIC, W.PERIODIC)),
+                                          (33, 11, 6, (W.OUTFLOW, W.PERIODIC)),
+                                          (65, 10, 8, (W.PERIODIC, W.OUTFLOW)),
+                                          (3, 2, 8, (W.OUTFLOW, W.OUTFLOW))])
+def test_staged_kernel_matches_generic_bitwise(D, orc, nx, ny, ns, bc):
+    """The species-staged kernel (each species copied into shared memory for
+    its moment sums and again for its update, two buffers, two cells per
+    thread) against the generic kernel after 6 FP32 steps, bit for bit, and
+    against the one-cell TMA kernel where that exists (S <= 4): grids of one
+    and several 64 x 8 tiles with ragged tails, odd nx, grids smaller than
+    the stencil, every boundary pairing, reaction (three species) and force
+    (two and four or more)."""
+    pb = W.random_smooth(nx, ny, ns, seed=23 + ns, reactive=ns == 3, force=ns != 3, bc=bc)
+    p, f0 = _noneq_f(orc, pb)
+    kerns = ("generic", "tma_staged") + (("tma_cell",) if ns <= 4 else ())
+    out = {}
+    for kern in kerns:
+        s = D.Solver(pb, "fp32", step_kernel=kern)
+        if kern == "tma_staged":
+            assert s.step_tile() == (64, 8, 2)
+        s.set_f(f0)
+        s.step(6)
+        out[kern] = s.get_f().cpu().numpy()
+        assert s.status()[0] == 0, kern
+        s.close()
+    for kern in kerns[1:]:
+        assert np.array_equal(out[kern], out["generic"]), kern
 
 
 # ---------------------------------------------------------------------------
