@@ -130,8 +130,8 @@ enum dbm_step_kernel {
                                  S = 1: one cell per thread; S = 2: all planes in one
                                  copy, two cells per thread on grids of at least 4096
                                  tiles of 64 x 8 cells, else one cell per thread;
-                                 S >= 3: as DBM_KERNEL_TMA_STAGED (with the thermo or
-                                 rounding option: one cell per thread, S <= 4)       */
+                                 S = 3, 4: one cell per thread; S >= 5: as
+                                 DBM_KERNEL_TMA_STAGED                               */
     DBM_KERNEL_TMA_CELL = 3,  /* TMA-staged, all planes in one copy, one cell per
                                  thread (S <= 4)                                     */
     DBM_KERNEL_TMA_PAIR = 4,  /* TMA-staged, two adjacent cells per thread: S = 2 all

@@ -57,17 +57,18 @@ static bool staged_supported(const dbm_params &p)
 
 // The tile of the TMA-staged step.  Two species: two cells per thread when
 // asked for, or (DBM_KERNEL_AUTO / DBM_KERNEL_TMA) on grids of at least
-// PAIR_MIN_TILES pair tiles, else the one-cell tile; the species-staged
-// kernel only when asked for.  Three or more species: the species-staged
-// kernel (two cells per thread) unless one cell per thread is asked for or
-// the arithmetic options are on (one-cell kernels, up to four species).
+// PAIR_MIN_TILES pair tiles, else the one-cell tile.  Three and four
+// species: the one-cell tile (faster than the species-staged kernel on every
+// grid measured), the species-staged one when two cells per thread are asked
+// for.  Five or more: the species-staged kernel, the only TMA-staged one.
 static void choose_tile(dbm_handle *h)
 {
     const dbm_params &p = h->p;
     const int want = p.step_kernel;
     h->tma_staged = 0;
-    if (staged_supported(p) &&
-        (want == DBM_KERNEL_TMA_STAGED || (p.nspecies >= 3 && want != DBM_KERNEL_TMA_CELL))) {
+    const bool staged_by_default = p.nspecies > 4 && want != DBM_KERNEL_TMA_CELL;
+    const bool staged_asked = want == DBM_KERNEL_TMA_STAGED || (p.nspecies >= 3 && want == DBM_KERNEL_TMA_PAIR);
+    if (staged_supported(p) && (staged_by_default || staged_asked)) {
         h->tma_staged = 1;
         h->tma_tx = STAGED_TX;
         h->tma_ty = STAGED_TY;

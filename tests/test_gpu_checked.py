@@ -35,7 +35,7 @@ CASES = [  # name, nx, ny, species, precision, kernel, boundaries
     ("four_37x13", 37, 13, 4, "fp32", "auto", PO),
     ("single_70x23", 70, 23, 1, "fp32", "auto", OP),
     ("generic_45x9_s5", 45, 9, 5, "fp32", "generic", PO),
-    ("cell_45x9_s3", 45, 9, 3, "fp32", "tma_cell", PP),
+    ("staged_45x9_s3", 45, 9, 3, "fp32", "tma_pair", PP),
     ("staged_67x9_s2", 67, 9, 2, "fp32", "tma_staged", OO),
     ("staged_45x9_s5", 45, 9, 5, "fp32", "auto", PO),
     ("staged_130x17_s8", 130, 17, 8, "fp32", "auto", OP),

@@ -33,7 +33,7 @@ def D():
     return dbm
 
 
-@pytest.mark.parametrize("ns,kernel", [(2, "tma_cell"), (2, "tma_pair"), (3, "tma_cell"), (3, "tma"),
+@pytest.mark.parametrize("ns,kernel", [(2, "tma_cell"), (2, "tma_pair"), (3, "tma"), (3, "tma_staged"),
                                        (2, "tma_staged"), (5, "tma")])
 def test_tile_wait_timeout_is_reported(D, orc, ns, kernel):
     pb = W.random_smooth(70, 20, ns, seed=5, reactive=ns == 3)

@@ -307,17 +307,18 @@ def test_pair_kernel_matches_generic(D, orc, nx, ny, bc, react, force):
 def test_step_tile_choice(D):
     """The handle's tile: two cells per thread for two species on grids of
     at least 4096 tiles of 64 x 8 cells (or when asked for), else one cell
-    per thread; the species-staged 64 x 8 two-cell tile for three or more
-    species (and for two when asked for); one cell per thread for three
-    species with an arithmetic option; no tile for the generic, FP64 and
-    BF16DEV steps."""
+    per thread; one cell per thread for three and four species, the
+    species-staged 64 x 8 two-cell tile for five or more (and for two to
+    four when asked for); no tile for the generic, FP64 and BF16DEV
+    steps."""
     kh = W.kh_shear_layer(2048, ny=1024)
     small = W.kh_shear_layer(1024)
     cases = [(kh, "fp32", "auto", (64, 8, 2)), (kh, "fp32", "tma_cell", (32, 7, 1)),
              (small, "fp32", "auto", (32, 7, 1)), (small, "fp32", "tma_pair", (64, 8, 2)),
              (small, "fp32", "generic", (0, 0, 0)), (small, "fp64", "auto", (0, 0, 0)),
              (small, "bf16dev", "auto", (0, 0, 0)),
-             (W.random_smooth(70, 23, 3), "fp32", "auto", (64, 8, 2)),
+             (W.random_smooth(70, 23, 3), "fp32", "auto", (32, 8, 1)),
+             (W.random_smooth(70, 23, 4), "fp32", "tma", (32, 6, 1)),
              (W.random_smooth(70, 23, 3), "fp32", "tma_cell", (32, 8, 1)),
              (W.random_smooth(70, 23, 4), "fp32", "tma_pair", (64, 8, 2)),
              (W.random_smooth(70, 23, 6), "fp32", "auto", (64, 8, 2)),
