@@ -47,8 +47,9 @@ from . import dbm as D
 from . import workloads as W
 
 # kernel configuration of the batched groups (tile shape, launch form, L2
-# promotion): what the tuner picks for instances of 288^2 and 512^2 cells
-DEFAULT_CONFIG = {"tile": (32, 16), "cells": 1, "persistent": 0, "promote": 1}
+# promotion): what the tuner picks for the 64-instance mix of sides 64 to
+# 512, and the fastest shape measured on instances of 256^2 to 4096^2
+DEFAULT_CONFIG = {"tile": (64, 4), "cells": 1, "persistent": 0, "promote": 1}
 
 
 class Admission:
