@@ -222,7 +222,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(pb_full, precision, seconds):
+def cpu_baseline(pb_full, precision, seconds, one_core=True):
     """The FP64 oracle as it stands, on the host cores, over a bounded
     sample of the workload: a window of the same grid (same species,
     parameters and initial fields) stepped a few times."""
@@ -243,21 +243,34 @@ def cpu_baseline(pb_full, precision, seconds):
                    T=pb_full.T[y0:y0 + ny, x0:x0 + nx])
     p = O.params_of(pb)
     f = O.init_feq(p, pb.rho_s, pb.ux, pb.uy, pb.T)
-    O.run(p, f, 1)  # start the OpenMP thread pool
-    t0 = time.perf_counter()
-    f, st = O.run(p, f, 1)
-    t1 = time.perf_counter()
-    per_step = max(t1 - t0, 1e-6)
-    steps = max(1, min(1000, int(seconds / per_step)))
-    t0 = time.perf_counter()
-    _, st2 = O.run(p, f, steps)
-    dt = time.perf_counter() - t0
-    if st or st2:
-        raise RuntimeError(f"oracle status {st}/{st2} on the CPU-baseline sample: the timing would be cut short")
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": nx * ny * pb.ns * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nx}x{ny} window of the {pb_full.nx}x{pb_full.ny} grid, {pb.ns} species, "
-                      f"{steps} FP64 steps in {dt:.1f} s (OpenMP over rows)"}
+
+    def timed(budget):
+        O.run(p, f, 1)  # start the OpenMP thread pool
+        t0 = time.perf_counter()
+        g, st = O.run(p, f, 1)
+        per_step = max(time.perf_counter() - t0, 1e-6)
+        steps = max(1, min(1000, int(budget / per_step)))
+        t0 = time.perf_counter()
+        _, st2 = O.run(p, g, steps)
+        dt = time.perf_counter() - t0
+        if st or st2:
+            raise RuntimeError(f"oracle status {st}/{st2} on the CPU-baseline sample: the timing would be cut short")
+        return steps, dt
+
+    cores = O.set_threads(0)
+    steps, dt = timed(seconds)
+    window = f"{nx}x{ny} window of the {pb_full.nx}x{pb_full.ny} grid, {pb.ns} species"
+    out = {"value": nx * ny * pb.ns * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{window}, {steps} FP64 steps in {dt:.1f} s (OpenMP over rows)"}
+    if one_core and cores > 1:  # the same sample on one core, for a quarter of the time
+        O.set_threads(1)
+        try:
+            s1, d1 = timed(seconds / 4)
+        finally:
+            O.set_threads(cores)
+        out["one_core"] = {"value": nx * ny * pb.ns * s1 / d1, "unit": UNIT, "cores": 1,
+                           "sample": f"{window}, {s1} FP64 steps in {d1:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -269,11 +282,11 @@ def run_reference(args):
     # each "step" of the reference arm is a bounded sample of the workload
     per = max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_baseline(pb, args.precision, per / 4)
+        cpu_baseline(pb, args.precision, per / 4, one_core=False)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(pb, args.precision, per))
+        vals.append(cpu_baseline(pb, args.precision, per, one_core=False))
     wall = time.perf_counter() - t0
     value = statistics.median(v["value"] for v in vals)
     cb = dict(vals[-1])

@@ -48,6 +48,9 @@
  * nx*ny cells, species-major.  All arithmetic is IEEE double; build with
  * -ffp-contract=off so that no multiply-add is fused.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -484,6 +487,20 @@ int orc_prepare(const orc_params *p, double *Minv)
  * d(v_y f)/dy], everything on the right taken at time n.  fin is the whole
  * field; fout holds only the region, [s][i][y - y0][x - x0].  Returns
  * status bits. */
+/* Threads of the OpenMP loops over rows (for timing the oracle on one core
+ * and on all of them; no effect on any result).  n > 0 sets the number;
+ * returns the number the next parallel loop uses (1 without OpenMP). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int orc_step_region(const orc_params *p, const double *Minv, const double *fin, double *fout,
                     int x0, int x1, int y0, int y1)
 {

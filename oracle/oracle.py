@@ -178,6 +178,8 @@ def lib():
         L.orc_moments.argtypes = [pp, dp, dp]
         L.orc_nonequilibrium.argtypes = [pp, dp, dp]
         L.orc_conservation.argtypes = [pp, dp, dp]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = C.c_int
         _lib = L
     return _lib
 
@@ -306,6 +308,12 @@ def init_feq(params: Params, rho_s, ux, uy, T) -> np.ndarray:
     if lib().orc_init_feq(C.byref(cp), _dp(rho_s), _dp(ux), _dp(uy), _dp(T), _dp(f)) != 0:
         raise np.linalg.LinAlgError("singular moment matrix")
     return f
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (n > 0 sets them; timing only);
+    returns the number in use."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def run(params: Params, f, nsteps: int) -> tuple[np.ndarray, int]:
