@@ -435,6 +435,20 @@ __device__ __forceinline__ void mixture_T_num(float W, float w, float ux, float 
     hi = s;
     lo = __fsub_rn(se, pe);
 }
+// The same numerator with u.u itself carried exactly (error-free products
+// and sum): the stochastic mode's energy targets use the exact u.u, and the
+// temperature has to see the same value, else each cell's collision moves
+// energy by (u.u - RN(u.u)) w, whose sign is systematic.
+__device__ __forceinline__ void mixture_T_num_exact(float W, float w, float ux, float uy, float &hi, float &lo)
+{
+    float xl, yl, e1, pe, se;
+    const float x2 = ff_prod(ux, ux, xl), y2 = ff_prod(uy, uy, yl);
+    const float u2 = ff_sum(x2, y2, e1);  // u.u = u2 + (e1 + xl + yl)
+    const float u2l = __fadd_rn(e1, __fadd_rn(xl, yl));
+    const float p = ff_prod(u2, w, pe);
+    hi = ff_sum(W, -p, se);  // W - u2 w = hi + se - pe
+    lo = __fsub_rn(__fsub_rn(se, pe), __fmul_rn(u2l, w));
+}
 __device__ __forceinline__ float mixture_T(float W, float w, float wd, float ux, float uy)
 {
     float hi, lo;
@@ -499,11 +513,15 @@ __device__ __forceinline__ float sr_fma(float a, float b, float c, float u)
     const float s = ff_sum(c, ff_prod(a, b, pe), se);
     return sr_ff(s, __fadd_rn(se, pe), u);
 }
-// The k-th uniform number in [0, 1) of a cell whose hash is h: a Weyl
-// sequence (golden-ratio increments) from h, top 24 bits.
+// The k-th uniform number in [0, 1) of a cell whose hash is h: the hash
+// of a golden-ratio Weyl sequence from h, top 24 bits.  A rounding's
+// residual depends on earlier roundings of the same cell (the store on the
+// temperature), so the numbers of one cell are hashed one by one rather
+// than taken as fixed shifts of the first, which would make a later number
+// a function of an earlier one.
 __device__ __forceinline__ float sr_uniform(unsigned h, int k)
 {
-    return __uint2float_rz((h + (unsigned)k * 0x9e3779b9u) >> 8) * 0x1p-24f;
+    return __uint2float_rz(mix32(h + (unsigned)k * 0x9e3779b9u) >> 8) * 0x1p-24f;
 }
 
 // Mixture u, T of one cell (reading R1 of the collision's conservation)
@@ -753,7 +771,7 @@ __device__ __forceinline__ void step_cell(const K &c, const G &g, const Tile &t,
                     L::set(T, j, sr_round(T64[j], sr_uniform(hcell[j], 0)));
                 } else {
                     float nh, nl;
-                    mixture_T_num(L::get(we, j), L::get(w, j), L::get(ux, j), L::get(uy, j), nh, nl);
+                    mixture_T_num_exact(L::get(we, j), L::get(w, j), L::get(ux, j), L::get(uy, j), nh, nl);
                     const float wdj = L::get(wd, j);
                     const float q = __fadd_rn(nh, nl) / wdj;
                     const float r = __fadd_rn(__fmaf_rn(-q, wdj, nh), nl);  // (nh + nl) - q wd
