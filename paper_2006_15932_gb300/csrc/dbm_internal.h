@@ -101,6 +101,7 @@ struct OutConsts {
 struct dbm_handle {
     dbm_params p;
     CUtensorMap tmap[2];  // TMA descriptors of the two bound state buffers
+    CUtensorMap tmap_in[2];  // the same with an interior box (species-staged moment sums)
     int tma_ok;           // the TMA-staged step kernel can run
     int tma_tx, tma_ty;   // its tile (cells) and cells per thread (1 or 2),
     int tma_cw;           // fixed at dbm_bind

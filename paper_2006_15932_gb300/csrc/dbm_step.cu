@@ -13,19 +13,21 @@ int launch_step_t(dbm_handle *h, const void *fin, void *fout, cudaStream_t st);
 template <int S, int TX, int TY, int CW, bool ACC>
 int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st);
 template <int S, int TX, int TY>
-int launch_step_staged_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st);
+int launch_step_staged_t(dbm_handle *h, const CUtensorMap *tmap, const CUtensorMap *tmap_in, const void *fin,
+                         void *fout, cudaStream_t st);
 
 // The species-staged step of the handle's tile (no arithmetic options).
-static int launch_staged(dbm_handle *h, const CUtensorMap *tm, const void *fin, void *fout, cudaStream_t st)
+static int launch_staged(dbm_handle *h, int cur, const void *fin, void *fout, cudaStream_t st)
 {
+    const CUtensorMap *tm = &h->tmap[cur], *ti = &h->tmap_in[cur];
     switch (h->p.nspecies) {
-    case 2: return launch_step_staged_t<2, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
-    case 3: return launch_step_staged_t<3, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
-    case 4: return launch_step_staged_t<4, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
-    case 5: return launch_step_staged_t<5, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
-    case 6: return launch_step_staged_t<6, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
-    case 7: return launch_step_staged_t<7, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
-    case 8: return launch_step_staged_t<8, STAGED_TX, STAGED_TY>(h, tm, fin, fout, st);
+    case 2: return launch_step_staged_t<2, STAGED_TX, STAGED_TY>(h, tm, ti, fin, fout, st);
+    case 3: return launch_step_staged_t<3, STAGED_TX, STAGED_TY>(h, tm, ti, fin, fout, st);
+    case 4: return launch_step_staged_t<4, STAGED_TX, STAGED_TY>(h, tm, ti, fin, fout, st);
+    case 5: return launch_step_staged_t<5, STAGED_TX, STAGED_TY>(h, tm, ti, fin, fout, st);
+    case 6: return launch_step_staged_t<6, STAGED_TX, STAGED_TY>(h, tm, ti, fin, fout, st);
+    case 7: return launch_step_staged_t<7, STAGED_TX, STAGED_TY>(h, tm, ti, fin, fout, st);
+    case 8: return launch_step_staged_t<8, STAGED_TX, STAGED_TY>(h, tm, ti, fin, fout, st);
     }
     return DBM_ERR_INVALID;
 }
@@ -122,6 +124,12 @@ int make_tensor_maps(dbm_handle *h)
         CUresult r = encode(&h->tmap[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->f[k], dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r == CUDA_SUCCESS && h->tma_staged) {  // interior box of one species: the moment-sum copies
+            cuuint32_t box_in[3] = {(cuuint32_t)h->tma_tx, (cuuint32_t)h->tma_ty, (cuuint32_t)Q};
+            r = encode(&h->tmap_in[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->f[k], dims, strides, box_in, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
         if (r != CUDA_SUCCESS) {
             h->tma_tx = h->tma_ty = h->tma_cw = h->tma_staged = 0;
             return DBM_OK;
@@ -153,7 +161,7 @@ int launch_step(dbm_handle *h, int cur, cudaStream_t st)
     const int want = h->p.step_kernel;
     if (h->tma_ok && want != DBM_KERNEL_GENERIC) {
         const CUtensorMap *tm = &h->tmap[cur];
-        if (h->tma_staged) return launch_staged(h, tm, fin, fout, st);
+        if (h->tma_staged) return launch_staged(h, cur, fin, fout, st);
         return uses_acc(h->p) ? launch_tma<true>(h, tm, fin, fout, st) : launch_tma<false>(h, tm, fin, fout, st);
     }
     if (uses_acc(h->p)) return DBM_ERR_INVALID;  // the options exist in the TMA-staged kernel only

@@ -1358,8 +1358,9 @@ int launch_step_tma_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, v
 // not grow with the species count: three and more species run two cells per
 // thread at two CTAs per SM (the all-species tile of three species in pairs
 // would hold one).  Each species is copied twice per tile: for its moment
-// sums (step 1 reads the tile's own cells) and for its update (the
-// stencil).  Use k = 0 .. 2S-1 takes species k mod S from buffer k & 1,
+// sums only its TX x TY own cells (a second descriptor, an interior box; no
+// halo), for its update the tile and its halo.  Use k = 0 .. 2S-1 takes
+// species k mod S from buffer k & 1,
 // whose mbarrier completes its phase k >> 1 with that copy; while a use is
 // computed the copy of the next one is in flight, and once every thread is
 // done with a buffer (the barrier in release) the leader refills it for use
@@ -1375,11 +1376,14 @@ template <int S, int TX, int TY>
 struct StagedTile2 {
     static constexpr bool kStaged = true;
     static constexpr int BX = TX + 8, BY = TY + 4, PS = BX * BY, NT = TX / 2 * TY;
+    static constexpr int PI = TX * TY;  // plane of an interior copy
     static constexpr unsigned BYTES = (unsigned)(PS * Q * sizeof(float));
+    static constexpr unsigned BYTES_IN = (unsigned)(PI * Q * sizeof(float));
     using V = float2;
     float *buf;         // buffer 0 (buffer 1 follows at Q * PS)
     const float *cell;  // buffer 0, plane 0, this thread's row and first column
-    unsigned long long tmap;
+    const float *own;   // the same cells in the interior layout [plane][TY][TX]
+    unsigned long long tmap, tmap_in;  // tile + halo box; interior box
     unsigned bar0;      // mbarrier of buffer 0 (buffer 1: bar0 + 8)
     const float *fin;
     int bx0, by0, nx, ny, pitch, bc_x, bc_y, wait_polls;
@@ -1388,15 +1392,20 @@ struct StagedTile2 {
     mutable int failed_at;  // the use whose wait ran out for good; 2S: none
 
     // view of use k: plane s * Q + i of species s read from buffer k & 1
+    // (interior layout for the moment sums, k < S)
     __device__ __forceinline__ SmemTile2 view(int k, int s) const
     {
+        if (k < S) return SmemTile2{own + (k & 1) * Q * PS - s * Q * PI, PI, TX, buf, 2 * Q * PS, flag};
         return SmemTile2{cell + ((k & 1) - s) * Q * PS, PS, BX, buf, 2 * Q * PS, flag};
     }
     __device__ __forceinline__ static bool leader() { return threadIdx.x == 0 && threadIdx.y == 0; }
     // leader: the copy of use k into its buffer
     __device__ __forceinline__ void issue(int k) const
     {
-        tma_tile_load(buf + (k & 1) * Q * PS, tmap, bx0, by0, bar0 + 8u * (k & 1), BYTES, (k % S) * Q);
+        if (k < S)  // interior box: origin at the tile's first cell
+            tma_tile_load(buf + (k & 1) * Q * PS, tmap_in, bx0 + GX, by0 + GY, bar0 + 8u * (k & 1), BYTES_IN, k * Q);
+        else
+            tma_tile_load(buf + (k & 1) * Q * PS, tmap, bx0, by0, bar0 + 8u * (k & 1), BYTES, (k - S) * Q);
     }
     __device__ __forceinline__ void acquire(int k) const
     {
@@ -1410,7 +1419,7 @@ struct StagedTile2 {
             }
         }
         const HaloSides hs = halo_sides<TX, TY>(bx0, by0, nx, ny);
-        if (hs.any())
+        if (k >= S && hs.any())
             halo_fill<Q, TX, TY, NT>(hs, buf + (k & 1) * Q * PS, fin + (long long)(k % S) * Q * plane, bx0, by0,
                                      nx, ny, pitch, plane, bc_x, bc_y, threadIdx.y * (TX / 2) + threadIdx.x, flag);
     }
@@ -1455,7 +1464,8 @@ struct StagedOut : StateOutNoImages {
 template <int S, int TX, int TY>
 __global__ void __launch_bounds__(TX / 2 * TY, staged_ctas_per_sm(TX, TY))
     k_step_staged(const __grid_constant__ StepConsts<float, S> c, const __grid_constant__ CUtensorMap tmap,
-                  const float *__restrict__ fin, float *__restrict__ fout, unsigned *__restrict__ flag)
+                  const __grid_constant__ CUtensorMap tmap_in, const float *__restrict__ fin,
+                  float *__restrict__ fout, unsigned *__restrict__ flag)
 {
     static_assert(S >= 2 && TX % 8 == 0, "two or more species; 16-byte aligned tile columns");
     using T = StagedTile2<S, TX, TY>;
@@ -1472,7 +1482,9 @@ __global__ void __launch_bounds__(TX / 2 * TY, staged_ctas_per_sm(TX, TY))
     __syncthreads();
     const T t{buf,
               buf + (ty + 2) * T::BX + (2 * tx + 4),
+              buf + ty * TX + 2 * tx,
               reinterpret_cast<unsigned long long>(&tmap),
+              reinterpret_cast<unsigned long long>(&tmap_in),
               b0,
               fin,
               (int)blockIdx.x * TX,
@@ -1501,7 +1513,8 @@ __global__ void __launch_bounds__(TX / 2 * TY, staged_ctas_per_sm(TX, TY))
 }
 
 template <int S, int TX, int TY>
-int launch_step_staged_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin, void *fout, cudaStream_t st)
+int launch_step_staged_t(dbm_handle *h, const CUtensorMap *tmap, const CUtensorMap *tmap_in, const void *fin,
+                         void *fout, cudaStream_t st)
 {
     constexpr size_t smem = (size_t)2 * (TX + 8) * (TY + 4) * Q * sizeof(float);
     static bool attr_set = false;  // per instantiation, set once per process
@@ -1515,7 +1528,7 @@ int launch_step_staged_t(dbm_handle *h, const CUtensorMap *tmap, const void *fin
     fill_step_consts<float, S>(h, c);
     dim3 block(TX / 2, TY);
     dim3 grid((h->p.nx + TX - 1) / TX, (h->p.ny + TY - 1) / TY);
-    k_step_staged<S, TX, TY><<<grid, block, smem, st>>>(c, *tmap, (const float *)fin, (float *)fout,
+    k_step_staged<S, TX, TY><<<grid, block, smem, st>>>(c, *tmap, *tmap_in, (const float *)fin, (float *)fout,
                                                          (unsigned *)h->scratch);
     return set_cuda_error(h, cudaGetLastError(), "staged step kernel launch");
 }

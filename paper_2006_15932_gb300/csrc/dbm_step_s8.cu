@@ -3,5 +3,6 @@
 
 namespace dbm {
 template int launch_step_t<8>(dbm_handle *, const void *, void *, cudaStream_t);
-template int launch_step_staged_t<8, STAGED_TX, STAGED_TY>(dbm_handle *, const CUtensorMap *, const void *, void *, cudaStream_t);
+template int launch_step_staged_t<8, STAGED_TX, STAGED_TY>(dbm_handle *, const CUtensorMap *, const CUtensorMap *,
+                                                                const void *, void *, cudaStream_t);
 }  // namespace dbm
