@@ -170,6 +170,47 @@ def test_eight_species(D, orc):
     assert rel_linf(s.get_f().cpu().numpy(), fr) <= FP64_TOL
 
 
+@pytest.mark.parametrize("ns,bc,force", [(5, (W.OUTFLOW, W.PERIODIC), True), (8, (W.PERIODIC, W.OUTFLOW), False)])
+def test_fp32_many_species_against_oracle(D, orc, ns, bc, force):
+    """Five and eight species in FP32 run the species-staged kernel (each
+    species through shared memory on its own) by default: 20 steps against
+    the oracle on a grid of two 64-wide tiles with ragged tails in x and y,
+    force on for five species."""
+    pb = W.random_smooth(70, 13, ns, seed=30 + ns, force=force, bc=bc)
+    p, f0 = _noneq_f(orc, pb)
+    s = D.Solver(pb, "fp32")
+    assert s.step_tile() == (64, 8, 2)
+    s.set_f(f0)
+    s.step(20)
+    f = s.get_f().cpu().numpy()
+    mom = s.moments().cpu().numpy()
+    assert s.status()[0] == 0
+    fr, _ = orc.run(p, f0, 20)
+    assert rel_linf(f, fr) <= FP32_TOL_F
+    errs = moments_errors(mom, orc.moments(p, fr), pb.ns)
+    assert np.all(errs <= 2e-4), errs
+
+
+def test_staged_full_size_one_step_sampled(D, orc):
+    """Six species on 1024 x 512 (1024 tiles of the species-staged kernel),
+    one step, against the oracle on sampled windows (edges and interior)."""
+    pb = W.random_smooth(1024, 512, 6, seed=36, bc=(W.OUTFLOW, W.PERIODIC))
+    s = D.Solver(pb, "fp32")
+    assert s.step_tile() == (64, 8, 2)
+    s.set_state()
+    f0 = s.get_f().cpu().numpy()
+    s.step(1)
+    f1 = s.get_f().cpu().numpy()
+    assert s.status()[0] == 0
+    s.close()
+    p = orc.params_of(pb)
+    rng = np.random.default_rng(1)
+    for (x0, x1, y0, y1) in _windows(pb.nx, pb.ny, rng, k=3, w=20):
+        want, st = orc.step_region(p, f0, x0, x1, y0, y1)
+        assert st == 0
+        assert rel_linf(f1[:, :, y0:y1, x0:x1], want) <= 1e-6, (x0, y0)
+
+
 def test_zero_steps_is_identity(D, orc):
     pb = W.random_smooth(10, 4, 2, seed=4)
     p, f0 = _noneq_f(orc, pb)
