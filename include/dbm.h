@@ -233,7 +233,8 @@ int dbm_scratch_bytes(const dbm_handle *h, size_t *bytes);
  * state.  The buffers must outlive every call that uses them.  Builds the
  * TMA descriptors of the two buffers and fixes the step's tile
  * (dbm_step_tile); DBM_ERR_INVALID when dbm_params.step_kernel asks for a
- * TMA-staged kernel that cannot run (not FP32, S > 4, no descriptor). */
+ * TMA-staged kernel that cannot run (not FP32; one cell per thread or an
+ * arithmetic option with S > 4; no descriptor). */
 int dbm_bind(dbm_handle *h, void *f_a, void *f_b, void *scratch);
 
 /* f = f^eq(n^s = rho^s / m^s, u, T) in every cell from the macroscopic
