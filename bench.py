@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="kh4096", choices=["kh4096", "reactive", "sod", "batched", "serve",
-                                                                    "precision_kh", "precision_reactive"])
+                                                                    "precision_kh", "precision_reactive", "smooth"])
+    ap.add_argument("--species", type=int, default=5,
+                    help="species of the smooth workload (seeded smooth fields; five or more run the species-staged kernel)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16dev"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and e2e side legs")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -67,10 +69,12 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name, grid=None):
+def make_workload(name, grid=None, species=5):
     from paper_2006_15932_gb300 import workloads as W
 
     nx, ny = (int(v) for v in grid.lower().split("x")) if grid else (None, None)
+    if name == "smooth":
+        return W.random_smooth(nx or 1024, ny or 1024, species, seed=W.SEED)
     if name == "kh4096":
         return W.kh_shear_layer(nx or 4096, ny=ny)
     if name == "reactive":
@@ -84,7 +88,7 @@ def workload_config(pb, name, precision):
     return {
         "workload": {"kh4096": "kelvin_helmholtz_shear_layer", "reactive": "reactive_premixed_2d",
                      "sod": "sod_shock_tube", "batched": "batched_shock_and_reactive_instances",
-                     "serve": "serve_poisson_request_mix"}[name],
+                     "serve": "serve_poisson_request_mix", "smooth": "random_smooth_fields"}[name],
         "grid": [pb.nx, pb.ny],
         "species": pb.ns,
         "velocities": 16,
@@ -133,6 +137,8 @@ def step_kernel_name(pb, precision, solver):
     if precision == "bf16dev":
         return f"k_step_bf16<{pb.ns},32,16,2>"
     tx, ty, cw = solver.step_tile()
+    if tx and cw == 2 and pb.ns >= 3:  # two cells per thread for three or more species: species-staged
+        return f"k_step_staged<{pb.ns},{tx},{ty}>"
     if tx:
         return f"k_step_tma<{pb.ns},{tx},{ty},{cw}>"
     return f"k_step<{pb.ns}>"
@@ -277,7 +283,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    pb = make_workload(args.workload, args.grid)
+    pb = make_workload(args.workload, args.grid, args.species)
     cfg = workload_config(pb, args.workload, args.precision)
     # each "step" of the reference arm is a bounded sample of the workload
     per = max(1.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
@@ -617,7 +623,7 @@ def main():
 
         solver = solvers[0]
     else:
-        pb = make_workload(args.workload, args.grid)
+        pb = make_workload(args.workload, args.grid, args.species)
         cfg = workload_config(pb, args.workload, args.precision)
         solver = D.Solver(pb, args.precision, device=dev, stream=stream)
         solver.set_state()
